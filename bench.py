@@ -1,0 +1,341 @@
+"""Benchmark: multigrid-preconditioned CG, DOF/s to relative residual 1e-8.
+
+One step = one full solve of the 257^3-vertex workload (log10 k ~ U[-2,2] on
+16^3 cell blocks, f ~ U[-1,1], 7 levels, V(2,2) with Chebyshev(2)-Jacobi,
+dense Cholesky on the 3^3 coarsest level, float64 CG to ||r|| <= 1e-8 ||f||)
+with inputs resident on the GPU.  The headline form runs the V-cycle in
+float32 inside the float64 CG; the plain float64 form and the bfloat16-
+coefficient form are timed the same way and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own independent problem (seed + rank):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mg_inputs as mi  # noqa: E402
+
+METRIC = "MG-PCG DOF/s to rel. residual 1e-8 (mixed vs FP64) and smoother HBM GB/s vs peak"
+WORKLOAD = "poisson257_c1e4"
+HEADLINE = "mixed_fp32"
+FORMS = ("mixed_fp32", "fp64", "mixed_bf16k")
+
+# Algorithmic HBM bytes per interior point for one launch of each kernel class,
+# as a function of the vector element size v, the three-coefficient bytes c and
+# the inverse-diagonal bytes v.  (Re-reads of neighbours served from cache are
+# not counted: each array is read once per point.)
+def bytes_per_point(cls: str, v: int, c: int, degree: int = 2) -> float:
+    return {
+        "cheb_zero": 3 * v + c + (v if degree > 2 else 0),  # read b, dinv, k; write x (and d)
+        "cheb_step": 5 * v + c,                           # read x, d|-, b, dinv, k; write x, d|-
+        "resid": 3 * v + c,                               # read x, b, k; write r
+        "restrict": 9 * v,                                # per coarse point: read 8 fine r, write 1
+        "prolong": 2 * v + v / 8,                         # read x, e/8; write x
+        "cg_dir": 16 + v,                                 # read z, p; write p (float64 p)
+        "cg_apply": 4 * 8 + 24,                           # read p, D, k64; write q (float64)
+        "cg_upd": 6 * 8 + v,                              # read x, r, p, q, z; write x, r
+        "dot": 8 + v,                                     # read r (float64), z
+        "cast": 12,                                       # float64 r -> float32 b
+    }[cls]
+
+
+def form_sizes(form: str):
+    return {"fp64": (8, 24), "mixed_fp32": (4, 12), "mixed_bf16k": (4, 6)}[form]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def config_dict(spec, n_ranks, iters=None):
+    N = spec["N"]
+    d = {
+        "workload": f"{WORKLOAD}: {N}^3 vertices ({(N - 2) ** 3} unknowns), log10 k ~ U[{spec['lo']:g},{spec['hi']:g}] "
+                    f"on {spec['block']}^3 cell blocks, f ~ U[-1,1], harmonic-mean edge k, 7 levels, "
+                    f"V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual {spec['rtol']:g}",
+        "precision": HEADLINE,
+        "l2": "no flush: inputs larger than L2 (each float64 vector 134 MB; working set > 2 GB)",
+        "parallelism": "replicas" if n_ranks > 1 else "single GPU",
+    }
+    if iters is not None:
+        d["iterations"] = iters
+    return d
+
+
+# ------------------------------------------------------------------ oracle arms
+def oracle_sample(spec, iters_to_tol: int, sample_iters: int):
+    """Time `sample_iters` oracle PCG iterations on the full workload; return
+    (DOF/s to tolerance, seconds, cores)."""
+    import oracle
+    dims = (spec["N"],) * 3
+    k = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], spec["seed"])
+    f = mi.rhs_f(dims, spec["seed"])
+    O = oracle.Oracle(k)
+    t = time.perf_counter()
+    O.pcg(f, 0.0, maxit=sample_iters)
+    dt = time.perf_counter() - t
+    n = (spec["N"] - 2) ** 3
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n / (dt / sample_iters * iters_to_tol), dt, cores
+
+
+def golden_iterations():
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_solves.json")) as fh:
+        return json.load(fh)[WORKLOAD]["iterations"]
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    spec = dict(mi.WORKLOADS[WORKLOAD])
+    its = golden_iterations()
+    sample = 4
+    vals, times = [], []
+    for s in range(args.warmup + args.steps):
+        v, dt, cores = oracle_sample(spec, its, sample)
+        if s >= args.warmup:
+            vals.append(v)
+            times.append(dt)
+    value = float(np.median(vals))
+    desc = (f"CPU FP64 oracle (assembled CSR, OpenMP) on the full {spec['N']}^3 workload: {sample} PCG iterations "
+            f"per step, scaled by its {its}-iteration count to tolerance")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(spec, 1, its),
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import paper_1604_07163_gb300 as mg
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    spec = dict(mi.WORKLOADS[WORKLOAD])
+    seed = spec["seed"] + rank
+    dims = (spec["N"],) * 3
+    n = (spec["N"] - 2) ** 3
+    k = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed), device=dev)
+    f_host = torch.tensor(mi.rhs_f(dims, seed)).pin_memory()
+    f = f_host.to(dev)
+    rtol = spec["rtol"]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    forms = {}
+    solutions = {}
+    roofline = clocks = None
+    launches = 0
+    for form in FORMS:
+        S = mg.MGSolver(k, mg.Params(precision=form, maxit=3000))
+        for _ in range(args.warmup):
+            x, st = S.solve(f, rtol)
+        headline = form == HEADLINE
+        if headline:
+            S.timing(True)
+            sampler = ClockSampler(dev.index if dev.index is not None else 0)
+            sampler.start()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        iters = []
+        launches_form = 0
+        for _ in range(args.steps):
+            x, st = S.solve(f, rtol)
+            iters.append(st.iters)
+            launches_form += st.kernel_launches
+        e1.record()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        forms[form] = {"value": world * n / (ms * 1e-3), "ms_per_step": ms, "iters": iters[-1],
+                       "true_rel_resid": st.true_rel_resid}
+        solutions[form] = x.detach().clone()
+        if headline:
+            clocks = sampler.stop()
+            launches = launches_form
+            kt = S.kernel_times()
+            S.timing(False)
+            roofline = roofline_from(kt, form)
+            forms[form]["kernel_ms_per_step"] = {f"{c}@L{l}": round(v[0] / args.steps, 4) for (c, l), v in kt.items()}
+            # end to end: pinned host f -> device, solve, x -> pinned host, every step
+            x_host = torch.empty(dims, dtype=torch.float64).pin_memory()
+            fd = torch.empty_like(f)
+            barrier()
+            e0.record()
+            for _ in range(args.steps):
+                fd.copy_(f_host, non_blocking=True)
+                xe, _ = S.solve(fd, rtol)
+                x_host.copy_(xe, non_blocking=True)
+            e1.record()
+            barrier()
+            ms_e2e = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+            e2e = {"value": world * n / (ms_e2e * 1e-3), "unit": "DOF/s",
+                   "h2d_bytes_per_step": f_host.numel() * 8, "d2h_bytes_per_step": x_host.numel() * 8}
+        S.close()
+        del S
+    ref = solutions["fp64"]
+    for form in FORMS:
+        if form != "fp64":
+            forms[form]["rel_err_vs_fp64_gpu"] = float((solutions[form] - ref).norm() / ref.norm())
+    speedup = forms["fp64"]["ms_per_step"] / forms[HEADLINE]["ms_per_step"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        its = forms["fp64"]["iters"]
+        sample = 20
+        v, dt, cores = oracle_sample(spec, its, sample)
+        cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+               "sample": f"{sample} PCG iterations of the CPU FP64 oracle on the full {spec['N']}^3 workload "
+                         f"({dt:.1f} s), scaled by the {its}-iteration count to tolerance"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": forms[HEADLINE]["value"], "unit": "DOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms[HEADLINE]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic", "config": config_dict(spec, world, forms[HEADLINE]["iters"]),
+        "forms": forms, "speedup_mixed_vs_fp64": speedup,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline_from(kt, form):
+    """Dominant level-0 kernel of the timed region: algorithmic GB/s vs the measured HBM peak."""
+    v, c = form_sizes(form)
+    peak, which = load_peaks()
+    best = None
+    for (cls, lvl), (ms, nl, pts) in kt.items():
+        if lvl != 0 or cls in ("bottom",):
+            continue
+        if best is None or ms > best[1]:
+            best = (cls, ms, nl, pts)
+    if best is None:
+        return None
+    cls, ms, nl, pts = best
+    bpp = bytes_per_point(cls, v, c)
+    if cls == "restrict":
+        bpp = 9 * v  # points counted on the coarse grid
+    avg_s = ms * 1e-3 / nl
+    traffic = bpp * pts / nl
+    achieved = traffic / avg_s / 1e9
+    return {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": which, "traffic": None,
+            "algorithmic_bytes_per_launch": traffic, "avg_launch_ms": ms / nl, "launches": nl}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

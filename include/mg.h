@@ -1,0 +1,194 @@
+/*
+ * mg.h -- C ABI of the GB300 multigrid-preconditioned CG library.
+ *
+ * The library solves A x = b (Eq. 1) where A is the 7-point discretisation of
+ * the heat-conduction operator -div(k grad phi) = f (Eq. 2) on a vertex-centred
+ * structured grid of the unit cube with zero Dirichlet boundary values.  The
+ * preconditioner is one geometric-multigrid V-cycle (Algorithm 1 applied
+ * recursively; per-level components of Sec. 2.1.1) with re-discretised coarse
+ * operators (Sec. 1, Sec. 4.3), a Jacobi-preconditioned Chebyshev smoother
+ * (Sec. 4.3), full-weighting restriction, trilinear prolongation, and an exact
+ * dense Cholesky solve of the coarsest operator (Sec. 1, Sec. 3.3.1).  Coarse
+ * levels too small to fill the GPU run on progressively fewer thread blocks and
+ * finally inside one persistent thread block: the single-GPU analogue of
+ * agglomerating a coarse problem onto fewer ranks (Sec. 3, Sec. 3.1).  The
+ * outer Krylov method is CG (Sec. 2.1), stopped when the residual 2-norm falls
+ * below rtol times that of b (Sec. 4.2, Sec. 4.3).
+ *
+ * Conventions shared by every entry point:
+ *  - Grids are given by their vertex counts Nx, Ny, Nz, boundary included.
+ *    Each N-1 must be divisible by 2^(levels-1); the coarsest level keeps at
+ *    least 3 interior points per axis and at most MG_MAX_COARSE unknowns.
+ *  - Nodal arrays (f, x, g, lambda, phi, ...) are dense C-order [z][y][x]
+ *    float64 arrays of Nz*Ny*Nx entries, x fastest.  Boundary entries of inputs
+ *    are ignored; boundary entries of outputs are written as 0.
+ *  - Cell arrays (k, gradients) are dense [z][y][x] float64 arrays of
+ *    (Nz-1)*(Ny-1)*(Nx-1) entries, cell (ci,cj,ck) having lower corner vertex
+ *    (ci,cj,ck).
+ *  - All array pointers are DEVICE pointers owned by the caller unless stated
+ *    otherwise; the library never frees them.  The handle owns its internal
+ *    level buffers and releases them in mg_free.
+ *  - Work is enqueued on the CUDA stream given to mg_setup (or mg_set_stream).
+ *    Entry points that return results to the host (mg_solve, the statistics)
+ *    synchronise that stream before returning; the step entry points do not.
+ *  - Every call returns an mg_status; no C++ exception crosses the ABI.  The
+ *    message of the last failure is available from mg_last_error.
+ */
+#ifndef MG_H
+#define MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_MAX_LEVELS 16
+#define MG_MAX_COARSE 1024
+
+typedef struct mg_handle mg_handle; /* opaque; owned by the library */
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_ARG = 1,             /* invalid argument (dims, levels, pointers, params) */
+  MG_ERR_ALLOC = 2,           /* device allocation failed */
+  MG_ERR_CUDA = 3,            /* a CUDA runtime call or kernel failed */
+  MG_ERR_NONFINITE = 4,       /* NaN/Inf in k, f or during the iteration */
+  MG_ERR_NOT_CONVERGED = 5,   /* maxit reached; x holds the last iterate */
+  MG_ERR_BREAKDOWN = 6,       /* CG breakdown: p.Ap <= 0 */
+  MG_ERR_DEVICE_TIMEOUT = 7,  /* a bounded on-device wait gave up */
+  MG_ERR_NOT_SPD = 8          /* coarsest operator not positive definite */
+} mg_status;
+
+typedef enum {
+  MG_FP64 = 0,        /* everything in float64 */
+  MG_MIXED_FP32 = 1,  /* V-cycle in float32 (vectors and coefficients) inside float64 CG */
+  MG_MIXED_BF16K = 2  /* V-cycle in float32 with bfloat16 edge coefficients inside float64 CG */
+} mg_precision;
+
+typedef struct {
+  int levels;          /* number of levels; 0 = coarsen until an axis has 3 interior points */
+  int nu_pre, nu_post; /* smoother sweeps before / after the coarse correction (default 1, 1) */
+  int cheby_degree;    /* Chebyshev iterations per sweep (default 2: "V(2,2), Chebyshev(2)") */
+  double eig_lo_frac;  /* interval [eig_lo_frac*eig_hi, eig_hi] for D^-1 A (default 0.1) */
+  double eig_hi;       /* upper end; 2.0 bounds the spectrum of D^-1 A (Gershgorin) */
+  int coarse_k_rule;   /* coarse cell k from its 8 children: 0 arithmetic (default), 1 geometric, 2 harmonic mean */
+  int face_rule;       /* edge k from the 4 cells sharing it: 0 harmonic mean (default), 1 arithmetic mean */
+  int k_is_log;        /* 1: k_cells holds ln k instead of k */
+  mg_precision precision;
+  int maxit;           /* CG iteration limit (default 1000) */
+  int nonzero_guess;   /* 1: mg_solve starts from the x passed in */
+  int flexible;        /* CG beta: 0 Fletcher-Reeves, 1 Polak-Ribiere (flexible); -1 = 0 for FP64, 1 for mixed */
+  int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
+  int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
+} mg_params;
+
+typedef struct {
+  int iters;             /* CG iterations performed */
+  double rel_resid;      /* recurrence residual ||r||/||b|| at exit */
+  double true_rel_resid; /* ||b - A x||/||b|| recomputed in float64 at exit */
+  double bnorm;          /* ||b||_2 over interior nodes */
+  double setup_s;        /* wall time of mg_setup */
+  double solve_s;        /* wall time of the last solve */
+  long long kernel_launches; /* kernels launched by the last solve (graph replays count their kernels) */
+} mg_stats;
+
+/* Fill p with the defaults listed above.  p must be non-NULL. */
+mg_status mg_params_default(mg_params* p);
+
+/* Build the level hierarchy for the conductivity field k_cells (one value per
+ * finest cell, > 0 and finite; ln k if p->k_is_log).  k_cells is a device
+ * pointer if k_on_device, else a host pointer; it is copied, not retained.
+ * stream is a cudaStream_t (NULL = default stream).  On success *h owns all
+ * device buffers of the hierarchy.  Setup follows Eq. 2 with the face rule of
+ * p->face_rule on every level and the coarse rule of p->coarse_k_rule between
+ * levels, and factors the coarsest operator with a dense Cholesky. */
+mg_status mg_setup(mg_handle** h, int Nx, int Ny, int Nz, const double* k_cells, int k_on_device,
+                   const mg_params* p, void* stream);
+
+/* Change the stream subsequent calls enqueue on. */
+mg_status mg_set_stream(mg_handle* h, void* stream);
+
+/* Solve A x = f by V-cycle-preconditioned CG until ||r|| <= rtol ||f||.
+ * f, x: device nodal arrays.  x is read as the initial guess only when the
+ * handle was built with nonzero_guess.  On MG_ERR_NOT_CONVERGED x holds the
+ * last iterate.  st may be NULL. */
+mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st);
+
+/* Adjoint solve A lambda = g (A is symmetric, so this is mg_solve on g), then,
+ * when grad_logk is non-NULL, the gradient of the loss whose derivative with
+ * respect to phi is g, taken with respect to the natural log of each finest
+ * cell's k:  dL/dln k_c = sum over the 12 edges e=(p,q) of cell c of
+ * -h_a^-2 (lambda_p - lambda_q)(phi_p - phi_q) dk_e/dln k_c.  phi is the
+ * forward solution (device nodal array, required when grad_logk is non-NULL).
+ * dL/df equals lambda.  grad_logk is a device cell array. */
+mg_status mg_solve_adjoint(mg_handle* h, const double* g, double* lambda, double rtol,
+                           const double* phi, double* grad_logk, mg_stats* st);
+
+/* Release every buffer the handle owns.  h may be NULL. */
+mg_status mg_free(mg_handle* h);
+
+/* Message of the last failure on this handle (or of the last failed
+ * mg_setup when h is NULL).  Valid until the next call on the handle. */
+const char* mg_last_error(const mg_handle* h);
+
+/* ---- introspection ------------------------------------------------------ */
+int mg_num_levels(const mg_handle* h);
+/* Vertex counts of level l (0 = finest) into N3 = {Nx, Ny, Nz}. */
+mg_status mg_level_dims(const mg_handle* h, int l, int* N3);
+/* Copy up to cap entries of the last solve's ||r_k||/||b|| history to the
+ * host array hist; returns the number available. */
+int mg_history(const mg_handle* h, double* hist, int cap);
+
+/* ---- step entry points (one row of the solve each; device nodal arrays of
+ * the level's size; computed in the hierarchy's V-cycle precision, inputs
+ * rounded to it and outputs widened to float64) -------------------------- */
+
+/* y = A_l x (Eq. 2 re-discretised on level l).  l = -1 selects the float64
+ * finest operator used by the outer CG whatever the precision. */
+mg_status mg_apply(mg_handle* h, int l, const double* x, double* y);
+/* One smoother sweep on level l: cheby_degree Chebyshev iterations for
+ * D^-1 A on [eig_lo_frac*eig_hi, eig_hi] (Sec. 4.3).  x is the initial guess
+ * unless zero_guess, and is overwritten with the result. */
+mg_status mg_smooth(mg_handle* h, int l, const double* b, double* x, int zero_guess);
+/* bc = R (b - A_l x): residual then full-weighting restriction R = P^T/8
+ * to level l+1 (Algorithm 1, restriction step). */
+mg_status mg_residual_restrict(mg_handle* h, int l, const double* b, const double* x, double* bc);
+/* x += P ec: trilinear prolongation from level l+1 to level l (Algorithm 1,
+ * prolongation step). */
+mg_status mg_prolong_add(mg_handle* h, int l, const double* ec, double* x);
+/* x = A_L^-1 b on the coarsest level by the dense Cholesky factor. */
+mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
+/* z = M^-1 r: one V-cycle with zero initial guess from the finest level. */
+mg_status mg_vcycle(mg_handle* h, const double* r, double* z);
+/* Cell gradient dL/dln k from phi and lambda (see mg_solve_adjoint). */
+mg_status mg_gradient(mg_handle* h, const double* phi, const double* lambda, double* grad_logk);
+/* ||f - A x||_2 on the float64 finest operator, written to *out (host). */
+mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, double* out);
+
+/* ---- kernel timing (opt-in, for benchmarks; not part of the method) ------
+ * When enabled, every kernel launch of the solve is bracketed by CUDA events
+ * on the launching stream and its device time is accumulated per kernel class
+ * and level.  Enabling or disabling resets the counters (and recaptures the
+ * V-cycle graph on next use). */
+typedef enum {
+  MG_K_CHEB_ZERO = 0,  /* smoother steps 0-1 from a zero guess (pre-smooth) */
+  MG_K_CHEB_STEP = 1,  /* smoother step with a materialised iterate */
+  MG_K_RESID = 2,      /* r = b - A x */
+  MG_K_RESTRICT = 3,   /* full weighting (points = coarse points) */
+  MG_K_PROLONG = 4,    /* x += P e */
+  MG_K_BOTTOM = 5,     /* telescoped single-block levels + coarse Cholesky solve */
+  MG_K_CG_DIR = 6,     /* p = z + beta p (float64) */
+  MG_K_CG_UPD = 7,     /* x += alpha p, r -= alpha q, r.r (float64) */
+  MG_K_DOT = 8,        /* r.z (float64 accumulation) */
+  MG_K_CAST = 9,       /* float64 residual -> float32 V-cycle right-hand side */
+  MG_K_CG_APPLY = 10,  /* q = A p, p.q with the float64 outer operator */
+  MG_K_NCLASS = 11
+} mg_kernel_class;
+mg_status mg_timing_enable(mg_handle* h, int on);
+/* Totals for class cls on level l (0 = finest): device milliseconds, number of
+ * launches and interior points processed (summed over launches). */
+mg_status mg_timing_read(const mg_handle* h, int cls, int l, double* ms, long long* launches, double* points);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -1,0 +1,995 @@
+// C ABI of the multigrid-preconditioned CG library (declarations and
+// argument conventions in include/mg.h).  Host side: level hierarchy,
+// launch geometry, the V-cycle driver (Algorithm 1 applied recursively),
+// the float64 PCG loop and the step entry points.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "mg.h"
+#include "mg_kernels.cuh"
+
+using namespace mgdev;
+
+namespace {
+
+struct LevelBuf {
+  Geom g{};
+  int N[3] = {0, 0, 0};
+  double ih2[3] = {0, 0, 0};       // h_a^-2
+  double* kc = nullptr;            // cell k (dense)
+  void *kx = nullptr, *ky = nullptr, *kz = nullptr;          // V-cycle precision
+  double *kx64 = nullptr, *ky64 = nullptr, *kz64 = nullptr;  // float64 copies
+  void* dinv = nullptr;
+  void* x[2] = {nullptr, nullptr};
+  void *d = nullptr, *b = nullptr, *r = nullptr;
+};
+
+std::string g_setup_error;
+
+}  // namespace
+
+struct mg_handle {
+  mg_params prm{};
+  cudaStream_t s = nullptr;   // internal non-blocking stream (graph capture needs one)
+  cudaStream_t us = nullptr;  // caller's stream; ordered against s with events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int nsm = 152;
+  int L = 0, lb = 0;  // levels; first level of the bottom kernel
+  LevelBuf lv[MG_MAX_LEVELS];
+  double* Lc = nullptr;  // Cholesky factor of the coarsest operator
+  int nc = 0;
+  double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cq = nullptr, *cp = nullptr;
+  double* cw = nullptr;    // float64 scratch (gradient input)
+  double* dg64 = nullptr;  // float64 diagonal of the finest operator
+  double* partials = nullptr;
+  int pstride = 0;
+  Scal* dsc = nullptr;
+  Scal* hsc = nullptr;  // pinned host mirror
+  int* dflag = nullptr;
+  std::vector<double> hist;
+  std::string err;
+  mg_stats st{};
+  std::vector<void*> allocs;
+  cudaGraphExec_t vexec = nullptr;
+  int vexec_zcur = 0;
+  long long launches = 0;        // kernels launched (counted at launch sites)
+  long long graph_launches = 0;  // kernels inside the captured V-cycle graph
+  // opt-in kernel timing
+  struct TRec {
+    int cls, level;
+    double pts;
+    int ev;  // index of the start event; ev + 1 is the stop event
+  };
+  bool timing = false;
+  bool capturing = false;
+  std::vector<cudaEvent_t> evpool;
+  int ev_graph_end = 0;  // events [0, ev_graph_end) belong to the captured graph
+  int ev_next = 0;
+  std::vector<TRec> graph_recs, pending;
+  double t_ms[MG_K_NCLASS][MG_MAX_LEVELS] = {};
+  long long t_n[MG_K_NCLASS][MG_MAX_LEVELS] = {};
+  double t_pts[MG_K_NCLASS][MG_MAX_LEVELS] = {};
+};
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+double secs(clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); }
+
+mg_status fail(mg_handle* h, mg_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_setup_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(h, MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define CKL() CK(cudaGetLastError())
+
+int roundup(int a, int m) { return (a + m - 1) / m * m; }
+
+Geom make_geom(int nx, int ny, int nz) {
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.Px = roundup(nx + 1, 8);
+  g.Py = ny + 1;
+  g.sz = (i64)g.Px * g.Py;
+  g.off = ((g.sz + g.Px + 1 + 31) / 32) * 32;
+  g.len = g.off + (i64)(nz + 1) * g.sz + 32;
+  return g;
+}
+
+int lin_blocks(const mg_handle* h, i64 n) {
+  i64 b = (n + 255) / 256;
+  i64 cap = (i64)h->nsm * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <class T> mg_status alloc(mg_handle* h, T** p, i64 n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MG_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(q);
+  e = cudaMemsetAsync(q, 0, (size_t)n * sizeof(T), h->s);
+  if (e != cudaSuccess) return fail(h, MG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  *p = (T*)q;
+  return MG_OK;
+}
+#define AL(ptr, T, n)                                  \
+  do {                                                 \
+    T* t_ = nullptr;                                   \
+    mg_status s_ = alloc<T>(h, &t_, (n));              \
+    if (s_ != MG_OK) return s_;                        \
+    ptr = t_;                                          \
+  } while (0)
+
+// ---- opt-in kernel timing: event pairs around launches, collected at sync points
+constexpr int EV_POOL = 2048;
+
+int tm_begin(mg_handle* h) {
+  if (!h->timing || h->ev_next + 2 > (int)h->evpool.size()) return -1;
+  const int e = h->ev_next;
+  h->ev_next += 2;
+  cudaEventRecordWithFlags(h->evpool[e], h->s, h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  return e;
+}
+
+void tm_end(mg_handle* h, int e, int cls, int level, double pts) {
+  if (e < 0) return;
+  cudaEventRecordWithFlags(h->evpool[e + 1], h->s, h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  mg_handle::TRec r{cls, level, pts, e};
+  if (h->capturing) h->graph_recs.push_back(r);
+  else h->pending.push_back(r);
+}
+
+void tm_collect(mg_handle* h) {
+  if (!h->timing) return;
+  for (const auto& r : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->evpool[r.ev], h->evpool[r.ev + 1]) == cudaSuccess) {
+      h->t_ms[r.cls][r.level] += ms;
+      h->t_n[r.cls][r.level] += 1;
+      h->t_pts[r.cls][r.level] += r.pts;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  h->pending.clear();
+  h->ev_next = h->ev_graph_end;
+}
+
+// z-marching launch geometry: 32x8 column tiles, planes split so that the
+// grid holds about 8 blocks per SM (levels too small for that get fewer blocks).
+dim3 zm_grid(const mg_handle* h, const Geom& g, int* kchunk) {
+  dim3 grid((g.nx + ZM_TX - 1) / ZM_TX, (g.ny + ZM_TY - 1) / ZM_TY, 1);
+  const int per = grid.x * grid.y;
+  const int target = h->nsm * 8;
+  int zs = (target + per - 1) / per;
+  zs = zs < 1 ? 1 : (zs > g.nz ? g.nz : zs);
+  int kc = (g.nz + zs - 1) / zs;
+  grid.z = (g.nz + kc - 1) / kc;
+  *kchunk = kc;
+  return grid;
+}
+
+template <bool RED, class Op>
+int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 0) {
+  int kc;
+  dim3 grid = zm_grid(h, g, &kc);
+  const int e = cls >= 0 ? tm_begin(h) : -1;
+  k_zmarch<Op, RED><<<grid, ZM_THREADS, 0, h->s>>>(op, g, kc, h->partials, h->pstride);
+  ++h->launches;
+  tm_end(h, e, cls, level, (double)g.npts());
+  return grid.x * grid.y * grid.z;
+}
+
+void finish(mg_handle* h, int nblocks, int mode) {
+  int flex = h->prm.flexible;
+  k_finish<<<1, 256, 0, h->s>>>(h->partials, nblocks, h->pstride, mode, h->dsc, flex);
+  ++h->launches;
+}
+
+int sweep_flips(int degree, bool zero) { return zero ? (degree == 1 ? 1 : degree - 1) : degree; }
+
+// Buffer index holding a level's result after pre- and post-smoothing.
+int level_result_cur(const mg_params& p) {
+  int f = 0;
+  for (int s = 0; s < p.nu_pre; ++s) f += sweep_flips(p.cheby_degree, s == 0);
+  for (int s = 0; s < p.nu_post; ++s) f += sweep_flips(p.cheby_degree, false);
+  return f & 1;
+}
+
+void cheb_consts(const mg_params& p, double* theta, double* delta, double* sigma) {
+  const double beta = p.eig_hi, alpha = p.eig_lo_frac * p.eig_hi;
+  *theta = 0.5 * (beta + alpha);
+  *delta = 0.5 * (beta - alpha);
+  *sigma = *theta / *delta;
+}
+
+template <class TV, class TC> struct Impl {
+  using TVt = TV;
+  using TCt = TC;
+  static TV* V(void* p) { return (TV*)p; }
+  static const TC* C(void* p) { return (const TC*)p; }
+
+  // One smoother sweep on level l starting from buffer cur; returns the new cur.
+  static int sweep(mg_handle* h, int l, int cur, bool zero) {
+    LevelBuf& Lv = h->lv[l];
+    const mg_params& p = h->prm;
+    double theta, delta, sigma;
+    cheb_consts(p, &theta, &delta, &sigma);
+    const TV inv_theta = (TV)(1.0 / theta);
+    double rho_prev = 1.0 / sigma;
+    int j0 = 0;
+    if (zero) {
+      if (p.cheby_degree == 1) {
+        OpChebZero1<TV, TV> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), inv_theta};
+        zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+        return cur ^ 1;
+      }
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      OpChebZero<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), p.cheby_degree > 2 ? V(Lv.d) : nullptr,
+                                C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(rho * rho_prev), (TV)(2.0 * rho / delta),
+                                inv_theta};
+      zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+      cur ^= 1;
+      rho_prev = rho;
+      j0 = 2;
+    }
+    for (int j = j0; j < p.cheby_degree; ++j) {
+      double c1 = 0.0, c2 = 0.0;
+      if (j > 0) {
+        const double rho = 1.0 / (2.0 * sigma - rho_prev);
+        c1 = rho * rho_prev;
+        c2 = 2.0 * rho / delta;
+        rho_prev = rho;
+      }
+      OpChebStep<TV, TV, TC> op{V(Lv.x[cur]), j > 0 ? V(Lv.d) : nullptr, V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]),
+                                j + 1 < p.cheby_degree ? V(Lv.d) : nullptr, C(Lv.kx), C(Lv.ky), C(Lv.kz),
+                                (TV)c1, (TV)c2, inv_theta};
+      zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
+      cur ^= 1;
+    }
+    return cur;
+  }
+
+  static void bottom(mg_handle* h, int l0) {
+    BotArgs<TV, TC> a{};
+    a.nlev = h->L - l0;
+    for (int l = l0; l < h->L; ++l) {
+      LevelBuf& Lv = h->lv[l];
+      BotLevel<TV, TC>& B = a.lv[l - l0];
+      B.g = Lv.g;
+      B.x[0] = V(Lv.x[0]);
+      B.x[1] = V(Lv.x[1]);
+      B.d = V(Lv.d);
+      B.b = V(Lv.b);
+      B.r = V(Lv.r);
+      B.dinv = V(Lv.dinv);
+      B.kx = C(Lv.kx);
+      B.ky = C(Lv.ky);
+      B.kz = C(Lv.kz);
+    }
+    a.nu_pre = h->prm.nu_pre;
+    a.nu_post = h->prm.nu_post;
+    a.degree = h->prm.cheby_degree;
+    cheb_consts(h->prm, &a.theta, &a.delta, &a.sigma);
+    a.Lc = h->Lc;
+    a.nc = h->nc;
+    const int e = tm_begin(h);
+    k_bottom<TV, TV, TC><<<1, BOT_THREADS, 0, h->s>>>(a);
+    ++h->launches;
+    tm_end(h, e, MG_K_BOTTOM, l0, (double)h->lv[l0].g.npts());
+  }
+
+  // V-cycle from level l with zero initial guess; b of level l must be set.
+  // Returns the buffer index of level l holding the result.
+  static int vcycle(mg_handle* h, int l) {
+    if (l >= h->lb) {
+      bottom(h, l);
+      return l == h->L - 1 ? 0 : level_result_cur(h->prm);
+    }
+    LevelBuf& Lv = h->lv[l];
+    LevelBuf& Cv = h->lv[l + 1];
+    int cur = 0;
+    for (int s = 0; s < h->prm.nu_pre; ++s) cur = sweep(h, l, cur, s == 0);
+    if (h->prm.nu_pre == 0) cudaMemsetAsync(Lv.x[0], 0, (size_t)Lv.g.len * sizeof(TV), h->s);
+    OpResidual<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)};
+    zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
+    OpRestrict<TV, TV> rs{Lv.g, V(Lv.r), V(Cv.b)};
+    zmarch<false>(h, Cv.g, rs, MG_K_RESTRICT, l);
+    const int ccur = vcycle(h, l + 1);
+    OpProlong<TV, TV> pr{Cv.g, V(Cv.x[ccur]), V(Lv.x[cur])};
+    zmarch<false>(h, Lv.g, pr, MG_K_PROLONG, l);
+    for (int s = 0; s < h->prm.nu_post; ++s) cur = sweep(h, l, cur, false);
+    return cur;
+  }
+
+  // z = M^-1 r on the float64 CG residual; returns the level-0 buffer (type TV)
+  // holding z.
+  static TV* precondition(mg_handle* h) {
+    LevelBuf& L0 = h->lv[0];
+    const bool mixed = h->prm.precision != MG_FP64;
+    if (mixed) {
+      const int e = tm_begin(h);
+      k_cast<TV, double><<<lin_blocks(h, L0.g.len), 256, 0, h->s>>>(h->cr, V(L0.b), L0.g.len);
+      ++h->launches;
+      tm_end(h, e, MG_K_CAST, 0, (double)L0.g.npts());
+    }
+    const int zc = vcycle(h, 0);
+    return V(L0.x[zc]);
+  }
+};
+
+template <class F> auto dispatch(mg_handle* h, F&& f) {
+  switch (h->prm.precision) {
+    case MG_MIXED_FP32: return f(Impl<float, float>{});
+    case MG_MIXED_BF16K: return f(Impl<float, __nv_bfloat16>{});
+    default: return f(Impl<double, double>{});
+  }
+}
+
+size_t vbytes(const mg_handle* h) { return h->prm.precision == MG_FP64 ? 8 : 4; }
+size_t cbytes(const mg_handle* h) {
+  return h->prm.precision == MG_FP64 ? 8 : (h->prm.precision == MG_MIXED_FP32 ? 4 : 2);
+}
+
+mg_status sync_check(mg_handle* h) {
+  CKL();
+  CK(cudaStreamSynchronize(h->s));
+  return MG_OK;
+}
+
+mg_status read_scal(mg_handle* h) {
+  CKL();
+  CK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(Scal), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  tm_collect(h);
+  return MG_OK;
+}
+
+// pack a dense float64 nodal array into a padded buffer of the level's vector type
+mg_status pack_level(mg_handle* h, int l, const double* src, void* dst, bool f64) {
+  const Geom& g = h->lv[l].g;
+  const int nb = lin_blocks(h, g.npts());
+  if (f64 || h->prm.precision == MG_FP64) k_pack<double><<<nb, 256, 0, h->s>>>(src, (double*)dst, g);
+  else k_pack<float><<<nb, 256, 0, h->s>>>(src, (float*)dst, g);
+  ++h->launches;
+  CKL();
+  return MG_OK;
+}
+
+mg_status unpack_level(mg_handle* h, int l, const void* src, double* dst, bool f64) {
+  const Geom& g = h->lv[l].g;
+  const int nb = lin_blocks(h, (i64)(g.nx + 2) * (g.ny + 2) * (g.nz + 2));
+  if (f64 || h->prm.precision == MG_FP64) k_unpack<double><<<nb, 256, 0, h->s>>>((const double*)src, dst, g);
+  else k_unpack<float><<<nb, 256, 0, h->s>>>((const float*)src, dst, g);
+  ++h->launches;
+  CKL();
+  return MG_OK;
+}
+
+mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k, int k_on_device) {
+  const mg_params& p = h->prm;
+  // level count
+  int N[3] = {Nx, Ny, Nz};
+  int L = p.levels;
+  if (L <= 0) {
+    L = 1;
+    int M[3] = {Nx, Ny, Nz};
+    while (L < MG_MAX_LEVELS) {
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) ok = ok && (M[a] - 1) % 2 == 0 && (M[a] - 1) / 2 + 1 >= 5;
+      if (!ok) break;
+      for (int a = 0; a < 3; ++a) M[a] = (M[a] - 1) / 2 + 1;
+      ++L;
+    }
+  }
+  if (L > MG_MAX_LEVELS) return fail(h, MG_ERR_ARG, "too many levels");
+  h->L = L;
+  for (int l = 0; l < L; ++l) {
+    LevelBuf& Lv = h->lv[l];
+    for (int a = 0; a < 3; ++a) {
+      if (N[a] < 3) return fail(h, MG_ERR_ARG, "level grid has fewer than 3 vertices on an axis");
+      Lv.N[a] = N[a];
+      Lv.ih2[a] = (double)(N[a] - 1) * (double)(N[a] - 1);
+    }
+    Lv.g = make_geom(N[0] - 2, N[1] - 2, N[2] - 2);
+    if (l + 1 < L)
+      for (int a = 0; a < 3; ++a) {
+        if ((N[a] - 1) % 2) return fail(h, MG_ERR_ARG, "N-1 not divisible by 2^(levels-1)");
+        N[a] = (N[a] - 1) / 2 + 1;
+      }
+  }
+  const Geom& gc = h->lv[L - 1].g;
+  h->nc = (int)gc.npts();
+  if (h->nc > MG_MAX_COARSE) return fail(h, MG_ERR_ARG, "coarsest level exceeds MG_MAX_COARSE unknowns");
+  // telescoping: first level whose unknowns fit the single-block bottom kernel
+  h->lb = L - 1;
+  while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
+
+  const bool mixed = p.precision != MG_FP64;
+  const size_t vb = vbytes(h), cb = cbytes(h);
+  // cells
+  for (int l = 0; l < L; ++l) {
+    LevelBuf& Lv = h->lv[l];
+    const i64 ncell = (i64)(Lv.N[0] - 1) * (Lv.N[1] - 1) * (Lv.N[2] - 1);
+    AL(Lv.kc, double, ncell);
+    if (l == 0) {
+      CK(cudaMemcpyAsync(Lv.kc, k, ncell * sizeof(double),
+                         k_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+      CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s));
+      k_cells_init<<<lin_blocks(h, ncell), 256, 0, h->s>>>(Lv.kc, ncell, p.k_is_log, h->dflag);
+      CKL();
+      int bad = 0;
+      CK(cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      if (bad) return fail(h, MG_ERR_NONFINITE, "k must be positive and finite in every cell");
+    } else {
+      const LevelBuf& F = h->lv[l - 1];
+      k_coarsen_cells<<<lin_blocks(h, ncell), 256, 0, h->s>>>(F.kc, Lv.kc, Lv.N[0] - 1, Lv.N[1] - 1, Lv.N[2] - 1,
+                                                              p.coarse_k_rule);
+      CKL();
+    }
+  }
+  // coefficients, diagonal and vectors per level
+  for (int l = 0; l < L; ++l) {
+    LevelBuf& Lv = h->lv[l];
+    const i64 n = Lv.g.len;
+    void* q;
+    for (void** c : {&Lv.kx, &Lv.ky, &Lv.kz}) {
+      AL(q, char, n * (i64)cb);
+      *c = q;
+    }
+    const bool need64 = !mixed || l == 0 || l == L - 1;
+    if (mixed && need64) {
+      AL(Lv.kx64, double, n);
+      AL(Lv.ky64, double, n);
+      AL(Lv.kz64, double, n);
+    } else if (!mixed) {
+      Lv.kx64 = (double*)Lv.kx;
+      Lv.ky64 = (double*)Lv.ky;
+      Lv.kz64 = (double*)Lv.kz;
+    }
+    const i64 nbox = (i64)(Lv.g.nx + 1) * (Lv.g.ny + 1) * (Lv.g.nz + 1);
+    const int nb = lin_blocks(h, nbox);
+    switch (p.precision) {
+      case MG_MIXED_FP32:
+        k_build_coef<float><<<nb, 256, 0, h->s>>>(Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule,
+                                                  (float*)Lv.kx, (float*)Lv.ky, (float*)Lv.kz, Lv.kx64, Lv.ky64,
+                                                  Lv.kz64);
+        break;
+      case MG_MIXED_BF16K:
+        k_build_coef<__nv_bfloat16><<<nb, 256, 0, h->s>>>(
+            Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule, (__nv_bfloat16*)Lv.kx,
+            (__nv_bfloat16*)Lv.ky, (__nv_bfloat16*)Lv.kz, Lv.kx64, Lv.ky64, Lv.kz64);
+        break;
+      default:
+        k_build_coef<double><<<nb, 256, 0, h->s>>>(Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule,
+                                                   (double*)Lv.kx, (double*)Lv.ky, (double*)Lv.kz, nullptr,
+                                                   nullptr, nullptr);
+    }
+    CKL();
+    AL(q, char, n * (i64)vb);
+    Lv.dinv = q;
+    const int nbi = lin_blocks(h, Lv.g.npts());
+    switch (p.precision) {
+      case MG_MIXED_FP32:
+        k_dinv<float, float, float><<<nbi, 256, 0, h->s>>>((float*)Lv.kx, (float*)Lv.ky, (float*)Lv.kz,
+                                                           (float*)Lv.dinv, Lv.g);
+        break;
+      case MG_MIXED_BF16K:
+        k_dinv<float, float, __nv_bfloat16><<<nbi, 256, 0, h->s>>>(
+            (__nv_bfloat16*)Lv.kx, (__nv_bfloat16*)Lv.ky, (__nv_bfloat16*)Lv.kz, (float*)Lv.dinv, Lv.g);
+        break;
+      default:
+        k_dinv<double, double, double><<<nbi, 256, 0, h->s>>>((double*)Lv.kx, (double*)Lv.ky, (double*)Lv.kz,
+                                                              (double*)Lv.dinv, Lv.g);
+    }
+    CKL();
+    for (void** v : {&Lv.x[0], &Lv.x[1], &Lv.d, &Lv.r}) {
+      AL(q, char, n * (i64)vb);
+      *v = q;
+    }
+    if (l > 0 || mixed) {
+      AL(q, char, n * (i64)vb);
+      Lv.b = q;
+    }
+  }
+  // outer CG vectors (float64, finest layout)
+  const i64 n0 = h->lv[0].g.len;
+  AL(h->cb, double, n0);
+  AL(h->cx, double, n0);
+  AL(h->cr, double, n0);
+  AL(h->cq, double, n0);
+  AL(h->cp, double, n0);
+  AL(h->cw, double, n0);
+  AL(h->dg64, double, n0);
+  {
+    const LevelBuf& L0 = h->lv[0];
+    k_diag64<<<lin_blocks(h, L0.g.npts()), 256, 0, h->s>>>(L0.kx64, L0.ky64, L0.kz64, h->dg64, L0.g);
+    CKL();
+  }
+  if (!mixed) h->lv[0].b = h->cr;  // the V-cycle's finest right-hand side is the CG residual
+  // reduction scratch: enough for every reducing launch on the finest level
+  int kcz;
+  dim3 gz = zm_grid(h, h->lv[0].g, &kcz);
+  h->pstride = gz.x * gz.y * gz.z;
+  AL(h->partials, double, 2 * (i64)h->pstride);
+  AL(h->dsc, Scal, 1);
+  // coarsest operator: dense float64 assembly and Cholesky factorisation
+  AL(h->Lc, double, (i64)h->nc * h->nc);
+  const LevelBuf& Cv = h->lv[L - 1];
+  k_assemble_dense<<<lin_blocks(h, h->nc), 256, 0, h->s>>>(Cv.kx64, Cv.ky64, Cv.kz64, Cv.g, h->Lc);
+  CKL();
+  CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s));
+  k_cholesky<<<1, 1024, 0, h->s>>>(h->Lc, h->nc, h->dflag);
+  CKL();
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (bad) return fail(h, MG_ERR_NOT_SPD, "coarsest operator is not positive definite");
+  return MG_OK;
+}
+
+void release(mg_handle* h) {
+  if (!h) return;
+  if (h->vexec) cudaGraphExecDestroy(h->vexec);
+  if (h->s) cudaStreamSynchronize(h->s);
+  for (void* p : h->allocs) cudaFree(p);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->s) cudaStreamDestroy(h->s);
+  if (h->dflag) cudaFree(h->dflag);
+  if (h->hsc) cudaFreeHost(h->hsc);
+  delete h;
+}
+
+// Runs the V-cycle (and, in mixed precision, the casts around it); through a
+// CUDA graph captured on first use when the handle enables graphs.
+template <class I, class TV> mg_status run_precondition(mg_handle* h, TV** z) {
+  if (!h->prm.use_graph) {
+    *z = I::precondition(h);
+    CKL();
+    return MG_OK;
+  }
+  if (!h->vexec) {
+    cudaGraph_t gr = nullptr;
+    tm_collect(h);
+    h->graph_recs.clear();
+    h->ev_next = 0;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    const long long before = h->launches;
+    TV* zp = I::precondition(h);
+    h->graph_launches = h->launches - before;
+    h->launches = before;
+    h->capturing = false;
+    h->ev_graph_end = h->ev_next;
+    cudaError_t e = cudaStreamEndCapture(h->s, &gr);
+    if (e != cudaSuccess) return fail(h, MG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->vexec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      h->vexec = nullptr;
+      return fail(h, MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    h->vexec_zcur = (zp == (TV*)h->lv[0].x[0]) ? 0 : 1;
+  }
+  CK(cudaGraphLaunch(h->vexec, h->s));
+  h->launches += h->graph_launches;
+  if (h->timing) h->pending.insert(h->pending.end(), h->graph_recs.begin(), h->graph_recs.end());
+  *z = (TV*)h->lv[0].x[h->vexec_zcur];
+  return MG_OK;
+}
+
+// Orders the internal stream after the caller's stream on entry and the
+// caller's stream after the internal one on exit.
+struct Guard {
+  mg_handle* h;
+  explicit Guard(mg_handle* hh) : h(hh) {
+    if (h) {
+      cudaEventRecord(h->ev_in, h->us);
+      cudaStreamWaitEvent(h->s, h->ev_in, 0);
+    }
+  }
+  ~Guard() {
+    if (h) {
+      cudaEventRecord(h->ev_out, h->s);
+      cudaStreamWaitEvent(h->us, h->ev_out, 0);
+    }
+  }
+};
+
+template <class I, bool FLEX, class TV>
+mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
+  // p = z + beta p;  q = A p, p.q -> alpha;  x += alpha p, r -= alpha q, r.r (and r.z_old)
+  zmarch<false>(h, g, OpPUpd<TV>{z, h->cp, h->dsc, 0.0}, MG_K_CG_DIR, 0);
+  int nb = zmarch<true>(h, g, OpApplyPQ{h->cp, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64}, MG_K_CG_APPLY, 0);
+  finish(h, nb, FIN_PQ);
+  nb = zmarch<true>(h, g, OpCgUpd<TV, FLEX>{h->cx, h->cr, h->cp, h->cq, z, h->dsc, 0.0}, MG_K_CG_UPD, 0);
+  finish(h, nb, FIN_RR);
+  return MG_OK;
+}
+
+template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  using TV = typename I::TVt;
+  auto t0 = clk::now();
+  const Geom& g = h->lv[0].g;
+  const LevelBuf& L0 = h->lv[0];
+  const mg_params& p = h->prm;
+  h->hist.clear();
+  const long long launches0 = h->launches;
+  mg_status s;
+  if ((s = pack_level(h, 0, f, h->cb, true)) != MG_OK) return s;
+  CK(cudaMemsetAsync(h->cx, 0, (size_t)g.len * 8, h->s));
+  CK(cudaMemsetAsync(h->cp, 0, (size_t)g.len * 8, h->s));
+  CK(cudaMemsetAsync(h->dsc, 0, sizeof(Scal), h->s));
+  int nb = zmarch<true>(h, g, OpDot<double>{h->cb, h->cb});
+  finish(h, nb, FIN_BB);
+  if (p.nonzero_guess) {
+    if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
+    OpResidual<double, double, double, double> res{h->cx, h->cb, h->cr, L0.kx64, L0.ky64, L0.kz64};
+    nb = zmarch<true>(h, g, res);
+    finish(h, nb, FIN_RR);
+  } else {
+    CK(cudaMemcpyAsync(h->cr, h->cb, (size_t)g.len * 8, cudaMemcpyDeviceToDevice, h->s));
+  }
+  if ((s = read_scal(h)) != MG_OK) return s;
+  Scal sc = *h->hsc;
+  mg_status result = MG_OK;
+  int it = 0;
+  const double bb = sc.bb;
+  if (sc.status & 1) return fail(h, MG_ERR_NONFINITE, "non-finite value in f or x");
+  const double tol2 = rtol * rtol * bb;
+  double rr = sc.rr;
+  if (bb > 0) h->hist.push_back(std::sqrt(rr / bb));
+  if (bb > 0 && rr > tol2) {
+    TV* z = nullptr;
+    if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
+    nb = zmarch<true>(h, g, OpDot<TV>{h->cr, z}, MG_K_DOT, 0);
+    finish(h, nb, FIN_RZ0);
+    for (it = 1; it <= p.maxit; ++it) {
+      if (p.flexible) cg_iteration<I, true>(h, z, g, L0);
+      else cg_iteration<I, false>(h, z, g, L0);
+      if ((s = read_scal(h)) != MG_OK) return s;
+      sc = *h->hsc;
+      if (sc.status & 1) {
+        result = fail(h, MG_ERR_NONFINITE, "non-finite value during the iteration");
+        break;
+      }
+      if (sc.status & 2) {
+        result = fail(h, MG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0");
+        break;
+      }
+      rr = sc.rr;
+      h->hist.push_back(std::sqrt(rr / bb));
+      if (rr <= tol2) break;
+      if (it == p.maxit) {
+        result = fail(h, MG_ERR_NOT_CONVERGED, "maximum number of iterations reached");
+        break;
+      }
+      if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
+      nb = zmarch<true>(h, g, OpDot<TV>{h->cr, z}, MG_K_DOT, 0);
+      finish(h, nb, FIN_RZ);
+    }
+    if (it > p.maxit) it = p.maxit;
+  }
+  if ((s = unpack_level(h, 0, h->cx, x, true)) != MG_OK) return s;
+  // true residual in float64
+  OpResidual<double, double, double, double> res{h->cx, h->cb, h->cq, L0.kx64, L0.ky64, L0.kz64};
+  nb = zmarch<true>(h, g, res);
+  finish(h, nb, FIN_TRUE);
+  if ((s = read_scal(h)) != MG_OK) return s;
+  h->st.iters = it;
+  h->st.bnorm = std::sqrt(bb);
+  h->st.rel_resid = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  h->st.true_rel_resid = bb > 0 ? std::sqrt(h->hsc->true_rr / bb) : 0.0;
+  h->st.solve_s = secs(t0);
+  h->st.kernel_launches = h->launches - launches0;
+  if (st) *st = h->st;
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_params_default(mg_params* p) {
+  if (!p) return MG_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->levels = 0;
+  p->nu_pre = 1;
+  p->nu_post = 1;
+  p->cheby_degree = 2;
+  p->eig_lo_frac = 0.1;
+  p->eig_hi = 2.0;
+  p->coarse_k_rule = 0;
+  p->face_rule = 0;
+  p->k_is_log = 0;
+  p->precision = MG_FP64;
+  p->maxit = 1000;
+  p->nonzero_guess = 0;
+  p->flexible = -1;
+  p->telescope_max_n = 4096;
+  p->use_graph = 1;
+  return MG_OK;
+}
+
+mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cells, int k_on_device,
+                   const mg_params* prm, void* stream) {
+  auto t0 = clk::now();
+  if (!out || !k_cells) return fail(nullptr, MG_ERR_ARG, "null handle or k pointer");
+  *out = nullptr;
+  mg_params p;
+  if (prm) p = *prm;
+  else mg_params_default(&p);
+  if (Nx < 3 || Ny < 3 || Nz < 3) return fail(nullptr, MG_ERR_ARG, "grid needs at least 3 vertices per axis");
+  if (p.nu_pre < 0 || p.nu_post < 0 || p.cheby_degree < 1 || p.maxit < 0 || !(p.eig_hi > 0) ||
+      !(p.eig_lo_frac > 0 && p.eig_lo_frac < 1) || p.coarse_k_rule < 0 || p.coarse_k_rule > 2 || p.face_rule < 0 ||
+      p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
+      p.levels > MG_MAX_LEVELS)
+    return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
+  if (p.flexible < 0) p.flexible = p.precision == MG_FP64 ? 0 : 1;
+  mg_handle* h = new (std::nothrow) mg_handle();
+  if (!h) return fail(nullptr, MG_ERR_ALLOC, "host allocation failed");
+  h->prm = p;
+  h->us = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (h->nsm <= 0) h->nsm = 152;
+  mg_status s = MG_OK;
+  if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    s = fail(h, MG_ERR_CUDA, "stream or event creation failed");
+  }
+  if (s == MG_OK && (cudaMalloc(&h->dflag, sizeof(int)) != cudaSuccess ||
+                     cudaMallocHost(&h->hsc, sizeof(Scal)) != cudaSuccess)) {
+    cudaGetLastError();
+    s = fail(h, MG_ERR_ALLOC, "scalar buffers");
+  }
+  Guard guard(s == MG_OK ? h : nullptr);
+  if (s == MG_OK) s = build_hierarchy(h, Nx, Ny, Nz, k_cells, k_on_device);
+  if (s != MG_OK) {
+    g_setup_error = h->err;
+    guard.h = nullptr;
+    release(h);
+    return s;
+  }
+  h->st.setup_s = secs(t0);
+  *out = h;
+  return MG_OK;
+}
+
+mg_status mg_set_stream(mg_handle* h, void* stream) {
+  if (!h) return MG_ERR_ARG;
+  h->us = (cudaStream_t)stream;
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  if (!h || !f || !x || !(rtol >= 0)) return h ? fail(h, MG_ERR_ARG, "null pointer or negative rtol") : MG_ERR_ARG;
+  Guard guard(h);
+  return dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, f, x, rtol, st); });
+}
+
+mg_status mg_gradient(mg_handle* h, const double* phi, const double* lambda, double* grad) {
+  if (!h || !phi || !lambda || !grad) return h ? fail(h, MG_ERR_ARG, "null pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  mg_status s;
+  if ((s = pack_level(h, 0, phi, h->cw, true)) != MG_OK) return s;
+  if ((s = pack_level(h, 0, lambda, h->cq, true)) != MG_OK) return s;
+  const LevelBuf& L0 = h->lv[0];
+  const i64 ncell = (i64)(L0.N[0] - 1) * (L0.N[1] - 1) * (L0.N[2] - 1);
+  k_gradient<<<lin_blocks(h, ncell), 256, 0, h->s>>>(L0.kc, h->cw, h->cq, L0.g, L0.ih2[0],
+                                                     L0.ih2[1], L0.ih2[2], h->prm.face_rule, grad);
+  CKL();
+  return MG_OK;
+}
+
+mg_status mg_solve_adjoint(mg_handle* h, const double* g, double* lambda, double rtol, const double* phi,
+                           double* grad_logk, mg_stats* st) {
+  if (!h || !g || !lambda || (grad_logk && !phi)) return h ? fail(h, MG_ERR_ARG, "null pointer") : MG_ERR_ARG;
+  mg_status s = mg_solve(h, g, lambda, rtol, st);
+  if (s != MG_OK) return s;
+  if (grad_logk) {
+    if ((s = mg_gradient(h, phi, lambda, grad_logk)) != MG_OK) return s;
+    return sync_check(h);
+  }
+  return MG_OK;
+}
+
+mg_status mg_free(mg_handle* h) {
+  if (!h) return MG_OK;
+  cudaStreamSynchronize(h->s);
+  release(h);
+  return MG_OK;
+}
+
+const char* mg_last_error(const mg_handle* h) { return h ? h->err.c_str() : g_setup_error.c_str(); }
+
+int mg_num_levels(const mg_handle* h) { return h ? h->L : 0; }
+
+mg_status mg_level_dims(const mg_handle* h, int l, int* N3) {
+  if (!h || !N3 || l < 0 || l >= h->L) return MG_ERR_ARG;
+  for (int a = 0; a < 3; ++a) N3[a] = h->lv[l].N[a];
+  return MG_OK;
+}
+
+int mg_history(const mg_handle* h, double* hist, int cap) {
+  if (!h) return 0;
+  const int n = (int)h->hist.size();
+  if (hist)
+    for (int i = 0; i < n && i < cap; ++i) hist[i] = h->hist[i];
+  return n;
+}
+
+mg_status mg_apply(mg_handle* h, int l, const double* x, double* y) {
+  if (!h || !x || !y || l < -1 || l >= h->L) return h ? fail(h, MG_ERR_ARG, "bad level or pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  mg_status s;
+  if (l < 0) {
+    const LevelBuf& L0 = h->lv[0];
+    if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
+    OpApply<double, double, double> op{h->cx, h->cq, L0.kx64, L0.ky64, L0.kz64};
+    zmarch<false>(h, L0.g, op);
+    CKL();
+    return unpack_level(h, 0, h->cq, y, true);
+  }
+  LevelBuf& Lv = h->lv[l];
+  if ((s = pack_level(h, l, x, Lv.x[0], false)) != MG_OK) return s;
+  dispatch(h, [&](auto impl) {
+    using I = decltype(impl);
+    using TV = std::remove_pointer_t<decltype(I::V(nullptr))>;
+    using TC = std::remove_const_t<std::remove_pointer_t<decltype(I::C(nullptr))>>;
+    OpApply<TV, TV, TC> op{I::V(Lv.x[0]), I::V(Lv.r), I::C(Lv.kx), I::C(Lv.ky), I::C(Lv.kz)};
+    zmarch<false>(h, Lv.g, op);
+    return 0;
+  });
+  CKL();
+  return unpack_level(h, l, Lv.r, y, false);
+}
+
+mg_status mg_smooth(mg_handle* h, int l, const double* b, double* x, int zero_guess) {
+  if (!h || !b || !x || l < 0 || l >= h->L) return h ? fail(h, MG_ERR_ARG, "bad level or pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  LevelBuf& Lv = h->lv[l];
+  mg_status s;
+  if ((s = pack_level(h, l, b, Lv.b, false)) != MG_OK) return s;
+  if (!zero_guess && (s = pack_level(h, l, x, Lv.x[0], false)) != MG_OK) return s;
+  const int cur = dispatch(h, [&](auto impl) { return decltype(impl)::sweep(h, l, 0, zero_guess != 0); });
+  CKL();
+  return unpack_level(h, l, Lv.x[cur], x, false);
+}
+
+mg_status mg_residual_restrict(mg_handle* h, int l, const double* b, const double* x, double* bc) {
+  if (!h || !b || !x || !bc || l < 0 || l + 1 >= h->L)
+    return h ? fail(h, MG_ERR_ARG, "bad level or pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  LevelBuf& Lv = h->lv[l];
+  LevelBuf& Cv = h->lv[l + 1];
+  mg_status s;
+  if ((s = pack_level(h, l, b, Lv.b, false)) != MG_OK) return s;
+  if ((s = pack_level(h, l, x, Lv.x[0], false)) != MG_OK) return s;
+  dispatch(h, [&](auto impl) {
+    using I = decltype(impl);
+    using TV = std::remove_pointer_t<decltype(I::V(nullptr))>;
+    using TC = std::remove_const_t<std::remove_pointer_t<decltype(I::C(nullptr))>>;
+    OpResidual<TV, TV, TV, TC> res{I::V(Lv.x[0]), I::V(Lv.b), I::V(Lv.r), I::C(Lv.kx), I::C(Lv.ky), I::C(Lv.kz)};
+    zmarch<false>(h, Lv.g, res);
+    OpRestrict<TV, TV> rs{Lv.g, I::V(Lv.r), I::V(Cv.b)};
+    zmarch<false>(h, Cv.g, rs);
+    return 0;
+  });
+  CKL();
+  return unpack_level(h, l + 1, Cv.b, bc, false);
+}
+
+mg_status mg_prolong_add(mg_handle* h, int l, const double* ec, double* x) {
+  if (!h || !ec || !x || l < 0 || l + 1 >= h->L) return h ? fail(h, MG_ERR_ARG, "bad level or pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  LevelBuf& Lv = h->lv[l];
+  LevelBuf& Cv = h->lv[l + 1];
+  mg_status s;
+  if ((s = pack_level(h, l + 1, ec, Cv.x[0], false)) != MG_OK) return s;
+  if ((s = pack_level(h, l, x, Lv.x[0], false)) != MG_OK) return s;
+  dispatch(h, [&](auto impl) {
+    using I = decltype(impl);
+    using TV = std::remove_pointer_t<decltype(I::V(nullptr))>;
+    OpProlong<TV, TV> pr{Cv.g, I::V(Cv.x[0]), I::V(Lv.x[0])};
+    zmarch<false>(h, Lv.g, pr);
+    return 0;
+  });
+  CKL();
+  return unpack_level(h, l, Lv.x[0], x, false);
+}
+
+mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x) {
+  if (!h || !b || !x) return h ? fail(h, MG_ERR_ARG, "null pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  const int l = h->L - 1;
+  LevelBuf& Lv = h->lv[l];
+  mg_status s;
+  if ((s = pack_level(h, l, b, Lv.b, false)) != MG_OK) return s;
+  dispatch(h, [&](auto impl) {
+    decltype(impl)::bottom(h, l);
+    return 0;
+  });
+  CKL();
+  return unpack_level(h, l, Lv.x[0], x, false);
+}
+
+mg_status mg_vcycle(mg_handle* h, const double* r, double* z) {
+  if (!h || !r || !z) return h ? fail(h, MG_ERR_ARG, "null pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  mg_status s;
+  if ((s = pack_level(h, 0, r, h->cr, true)) != MG_OK) return s;
+  void* zp = dispatch(h, [&](auto impl) { return (void*)decltype(impl)::precondition(h); });
+  CKL();
+  return unpack_level(h, 0, zp, z, false);
+}
+
+mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, double* out) {
+  if (!h || !f || !x || !out) return h ? fail(h, MG_ERR_ARG, "null pointer") : MG_ERR_ARG;
+  Guard guard(h);
+  const LevelBuf& L0 = h->lv[0];
+  mg_status s;
+  if ((s = pack_level(h, 0, f, h->cb, true)) != MG_OK) return s;
+  if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
+  OpResidual<double, double, double, double> res{h->cx, h->cb, h->cq, L0.kx64, L0.ky64, L0.kz64};
+  const int nb = zmarch<true>(h, L0.g, res);
+  finish(h, nb, FIN_TRUE);
+  if ((s = read_scal(h)) != MG_OK) return s;
+  *out = std::sqrt(h->hsc->true_rr);
+  return MG_OK;
+}
+
+mg_status mg_timing_enable(mg_handle* h, int on) {
+  if (!h) return MG_ERR_ARG;
+  CK(cudaStreamSynchronize(h->s));
+  if (on && h->evpool.empty()) {
+    h->evpool.resize(EV_POOL);
+    for (auto& e : h->evpool) CK(cudaEventCreate(&e));
+  }
+  if (h->vexec) {
+    cudaGraphExecDestroy(h->vexec);
+    h->vexec = nullptr;
+  }
+  h->timing = on != 0;
+  h->graph_recs.clear();
+  h->pending.clear();
+  h->ev_graph_end = h->ev_next = 0;
+  std::memset(h->t_ms, 0, sizeof(h->t_ms));
+  std::memset(h->t_n, 0, sizeof(h->t_n));
+  std::memset(h->t_pts, 0, sizeof(h->t_pts));
+  return MG_OK;
+}
+
+mg_status mg_timing_read(const mg_handle* h, int cls, int l, double* ms, long long* launches, double* points) {
+  if (!h || cls < 0 || cls >= MG_K_NCLASS || l < 0 || l >= MG_MAX_LEVELS) return MG_ERR_ARG;
+  if (ms) *ms = h->t_ms[cls][l];
+  if (launches) *launches = h->t_n[cls][l];
+  if (points) *points = h->t_pts[cls][l];
+  return MG_OK;
+}
+
+}  // extern "C"

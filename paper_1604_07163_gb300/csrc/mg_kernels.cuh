@@ -1,0 +1,491 @@
+// Kernels of the multigrid-preconditioned CG solve (see mg_device.cuh for the
+// data layout and the per-point operations).
+#pragma once
+#include "mg_device.cuh"
+
+namespace mgdev {
+
+constexpr int ZM_THREADS = 256;  // z-marching tile: 32 (x) by 8 (y) columns
+constexpr int ZM_TX = 32, ZM_TY = 8;
+
+// Multi-block z-marching driver: each thread owns one (i, j) column of a
+// 32 x 8 tile and walks planes [k0, k1).  With RED the per-thread sums are
+// reduced per block and written to partials[blockLinear] (and
+// partials[stride + blockLinear] for the second sum).
+template <class Op, bool RED>
+__global__ void __launch_bounds__(ZM_THREADS) k_zmarch(Op op, Geom g, int kchunk, double* partials, int stride) {
+  op.prepare();
+  const int i = blockIdx.x * ZM_TX + (threadIdx.x & 31);
+  const int j = blockIdx.y * ZM_TY + (threadIdx.x >> 5);
+  const int k0 = blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, g.nz);
+  double a0 = 0.0, a1 = 0.0;
+  if (i < g.nx && j < g.ny) {
+    i64 p = g.at(i, j, k0);
+    for (int k = k0; k < k1; ++k, p += g.sz) op.template pt<true>(g, i, j, k, p, a0, a1);
+  }
+  if constexpr (RED) {
+    block_sum2<ZM_THREADS>(a0, a1);
+    if (threadIdx.x == 0) {
+      const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      partials[b] = a0;
+      partials[stride + b] = a1;
+    }
+  }
+}
+
+// Single-block loop over all interior points of g (used inside the bottom kernel).
+template <class Op>
+__device__ __forceinline__ void block_for(const Op& op, const Geom& g) {
+  const i64 n = g.npts();
+  double a0 = 0, a1 = 0;
+  for (i64 t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const i64 r = t / g.nx;
+    const int j = (int)(r % g.ny);
+    const int k = (int)(r / g.ny);
+    op.template pt<false>(g, i, j, k, g.at(i, j, k), a0, a1);
+  }
+}
+
+// ------------------------------------------------------------ layout conversion
+// dense full-grid float64 (Nz,Ny,Nx) -> padded interior array of type T
+template <class T>
+__global__ void k_pack(const double* __restrict__ src, T* __restrict__ dst, Geom g) {
+  const i64 n = g.npts();
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const i64 r = t / g.nx;
+    const int j = (int)(r % g.ny);
+    const int k = (int)(r / g.ny);
+    const int Nx = g.nx + 2, Ny = g.ny + 2;
+    dst[g.at(i, j, k)] = store_as<T>(src[((i64)(k + 1) * Ny + (j + 1)) * Nx + (i + 1)]);
+  }
+}
+
+// padded interior array of type T -> dense full-grid float64 with zero boundary
+template <class T>
+__global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, Geom g) {
+  const int Nx = g.nx + 2, Ny = g.ny + 2, Nz = g.nz + 2;
+  const i64 n = (i64)Nx * Ny * Nz;
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int I = (int)(t % Nx);
+    const i64 r = t / Nx;
+    const int J = (int)(r % Ny);
+    const int K = (int)(r / Ny);
+    const bool in = I >= 1 && I <= g.nx && J >= 1 && J <= g.ny && K >= 1 && K <= g.nz;
+    dst[t] = in ? cvt<double>(src[g.at(I - 1, J - 1, K - 1)]) : 0.0;
+  }
+}
+
+// elementwise conversion of whole padded arrays (pads stay zero)
+template <class TD, class TS>
+__global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, i64 n) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    dst[t] = store_as<TD>(cvt<double>(src[t]));
+}
+
+// ------------------------------------------------------------ setup
+// k (or ln k) per cell -> k, with a flag for non-positive / non-finite values.
+__global__ void k_cells_init(double* kc, i64 n, int is_log, int* bad) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    double v = kc[t];
+    if (is_log) v = exp(v);
+    if (!(v > 0.0) || !isfinite(v)) atomicOr(bad, 1);
+    kc[t] = v;
+  }
+}
+
+// Coarse cell k as a mean of its 8 children: 0 arithmetic, 1 geometric, 2 harmonic.
+__global__ void k_coarsen_cells(const double* __restrict__ kf, double* __restrict__ kc, int cx, int cy, int cz,
+                                int rule) {
+  const i64 n = (i64)cx * cy * cz;
+  const int fx = 2 * cx, fy = 2 * cy;
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int ci = (int)(t % cx);
+    const i64 r = t / cx;
+    const int cj = (int)(r % cy);
+    const int ck = (int)(r / cy);
+    double s = 0.0;
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const double v = kf[((i64)(2 * ck + c) * fy + (2 * cj + b)) * fx + (2 * ci + a)];
+          s += rule == 0 ? v : rule == 1 ? log(v) : 1.0 / v;
+        }
+    kc[t] = rule == 0 ? s * 0.125 : rule == 1 ? exp(s * 0.125) : 8.0 / s;
+  }
+}
+
+// Mean of the 4 cells sharing an edge: harmonic (face_rule 0) or arithmetic.
+__device__ __forceinline__ double edge_mean(double a, double b, double c, double d, int face_rule) {
+  return face_rule ? 0.25 * ((a + b) + (c + d)) : 4.0 / ((1.0 / a + 1.0 / b) + (1.0 / c + 1.0 / d));
+}
+
+// Edge coefficients h_a^-2 k_e into the padded layout.  Thread (i,j,k) over
+// [-1,nx) x [-1,ny) x [-1,nz) writes the +x edge of point (i,j,k) when j,k are
+// interior, the +y edge when i,k are, the +z edge when i,j are.  Cells are the
+// dense (nz+1)(ny+1)(nx+1) array of this level.
+template <class TC>
+__global__ void k_build_coef(const double* __restrict__ kc, Geom g, double ihx2, double ihy2, double ihz2,
+                             int face_rule, TC* kx, TC* ky, TC* kz, double* kx64, double* ky64, double* kz64) {
+  const int bx = g.nx + 1, by = g.ny + 1, bz = g.nz + 1;
+  const i64 n = (i64)bx * by * bz;
+  const int cx = g.nx + 1, cy = g.ny + 1;  // cells per axis
+  auto cell = [&](int ci, int cj, int ck) { return kc[((i64)ck * cy + cj) * cx + ci]; };
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int i = (int)(t % bx) - 1;
+    const i64 r = t / bx;
+    const int j = (int)(r % by) - 1;
+    const int k = (int)(r / by) - 1;
+    const i64 p = g.at(i, j, k);
+    if (j >= 0 && k >= 0) {  // edge (i,j,k)-(i+1,j,k): cells (i+1, j..j+1, k..k+1)
+      const double v = ihx2 * edge_mean(cell(i + 1, j, k), cell(i + 1, j + 1, k), cell(i + 1, j, k + 1),
+                                        cell(i + 1, j + 1, k + 1), face_rule);
+      if (kx) kx[p] = store_as<TC>(v);
+      if (kx64) kx64[p] = v;
+    }
+    if (i >= 0 && k >= 0) {  // edge (i,j,k)-(i,j+1,k): cells (i..i+1, j+1, k..k+1)
+      const double v = ihy2 * edge_mean(cell(i, j + 1, k), cell(i + 1, j + 1, k), cell(i, j + 1, k + 1),
+                                        cell(i + 1, j + 1, k + 1), face_rule);
+      if (ky) ky[p] = store_as<TC>(v);
+      if (ky64) ky64[p] = v;
+    }
+    if (i >= 0 && j >= 0) {  // edge (i,j,k)-(i,j,k+1): cells (i..i+1, j..j+1, k+1)
+      const double v = ihz2 * edge_mean(cell(i, j, k + 1), cell(i + 1, j, k + 1), cell(i, j + 1, k + 1),
+                                        cell(i + 1, j + 1, k + 1), face_rule);
+      if (kz) kz[p] = store_as<TC>(v);
+      if (kz64) kz64[p] = v;
+    }
+  }
+}
+
+// float64 diagonal D = sum of the 6 float64 edge coefficients (outer operator)
+__global__ void k_diag64(const double* kx, const double* ky, const double* kz, double* dg, Geom g) {
+  const i64 n = g.npts();
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const i64 r = t / g.nx;
+    const int j = (int)(r % g.ny);
+    const int k = (int)(r / g.ny);
+    const i64 p = g.at(i, j, k);
+    dg[p] = ((kx[p - 1] + kx[p]) + (ky[p - g.Px] + ky[p])) + (kz[p - g.sz] + kz[p]);
+  }
+}
+
+// dinv = 1 / sum of the 6 stored edge coefficients (summed in precision R)
+template <class R, class TV, class TC>
+__global__ void k_dinv(const TC* kx, const TC* ky, const TC* kz, TV* dinv, Geom g) {
+  const i64 n = g.npts();
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const i64 r = t / g.nx;
+    const int j = (int)(r % g.ny);
+    const int k = (int)(r / g.ny);
+    const i64 p = g.at(i, j, k);
+    const R D = ((cvt<R>(kx[p - 1]) + cvt<R>(kx[p])) + (cvt<R>(ky[p - g.Px]) + cvt<R>(ky[p]))) +
+                (cvt<R>(kz[p - g.sz]) + cvt<R>(kz[p]));
+    dinv[p] = store_as<TV>((R)1 / D);
+  }
+}
+
+// Dense float64 operator of a (small) level in compact interior numbering.
+__global__ void k_assemble_dense(const double* kx, const double* ky, const double* kz, Geom g, double* A) {
+  const int n = (int)g.npts();
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const int i = u % g.nx, j = (u / g.nx) % g.ny, k = u / (g.nx * g.ny);
+    const i64 p = g.at(i, j, k);
+    double* row = A + (i64)u * n;
+    for (int v = 0; v < n; ++v) row[v] = 0.0;
+    const double c[6] = {kx[p - 1], kx[p], ky[p - g.Px], ky[p], kz[p - g.sz], kz[p]};
+    row[u] = ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+    if (i > 0) row[u - 1] = -c[0];
+    if (i < g.nx - 1) row[u + 1] = -c[1];
+    if (j > 0) row[u - g.nx] = -c[2];
+    if (j < g.ny - 1) row[u + g.nx] = -c[3];
+    if (k > 0) row[u - g.nx * g.ny] = -c[4];
+    if (k < g.nz - 1) row[u + g.nx * g.ny] = -c[5];
+  }
+}
+
+// In-place right-looking Cholesky of the dense n x n matrix A (lower triangle
+// receives L; the strict upper triangle is zeroed).  One block.  Sets *bad if
+// a pivot is not positive.
+__global__ void k_cholesky(double* A, int n, int* bad) {
+  __shared__ double piv;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double a = A[(i64)j * n + j];
+      if (!(a > 0.0)) *bad = 1;
+      piv = a > 0.0 ? sqrt(a) : 1.0;
+      A[(i64)j * n + j] = piv;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(i64)i * n + j] /= piv;
+    __syncthreads();
+    const i64 m = (i64)(n - j - 1);
+    for (i64 t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int ii = j + 1 + (int)(t / m), kk = j + 1 + (int)(t % m);
+      if (kk <= ii) A[(i64)ii * n + kk] -= A[(i64)ii * n + j] * A[(i64)kk * n + j];
+    }
+    __syncthreads();
+  }
+  for (i64 t = threadIdx.x; t < (i64)n * n; t += blockDim.x)
+    if (t % n > t / n) A[t] = 0.0;
+}
+
+// ------------------------------------------------------------ scalars
+enum FinishMode { FIN_BB = 0, FIN_RR = 1, FIN_RZ0 = 2, FIN_PQ = 3, FIN_RZ = 4, FIN_TRUE = 5 };
+
+// Sums partials[0..n) (and partials[stride..stride+n)) in a fixed order and
+// updates the CG scalars.  One block of 256 threads.
+__global__ void __launch_bounds__(256) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
+                                                int flexible) {
+  double a0 = 0.0, a1 = 0.0;
+  for (int t = threadIdx.x; t < n; t += 256) {
+    a0 += partials[t];
+    a1 += partials[stride + t];
+  }
+  block_sum2<256>(a0, a1);
+  if (threadIdx.x != 0) return;
+  switch (mode) {
+    case FIN_BB:
+      s->bb = a0;
+      s->rr = a0;
+      if (!isfinite(a0)) s->status |= 1;
+      break;
+    case FIN_RR:
+      s->rr = a0;
+      s->rz_old = a1;
+      if (!isfinite(a0)) s->status |= 1;
+      break;
+    case FIN_TRUE:
+      s->true_rr = a0;
+      break;
+    case FIN_RZ0:
+      s->rho = a0;
+      s->beta = 0.0;
+      if (!isfinite(a0)) s->status |= 1;
+      break;
+    case FIN_PQ:
+      s->pq = a0;
+      if (!(a0 > 0.0)) s->status |= isfinite(a0) ? 2 : 1;
+      s->alpha = a0 > 0.0 ? s->rho / a0 : 0.0;
+      break;
+    case FIN_RZ: {
+      // Fletcher-Reeves: beta = rho_new / rho.  Polak-Ribiere (flexible):
+      // beta = (rho_new - r_new.z_old) / rho.
+      s->beta = flexible ? (a0 - s->rz_old) / s->rho : a0 / s->rho;
+      s->rho_new = a0;
+      s->rho = a0;
+      if (!isfinite(a0)) s->status |= 1;
+      break;
+    }
+  }
+}
+
+// ------------------------------------------------------------ gradient
+// dL/dln k_c for every finest cell from phi and lambda (padded float64):
+//   sum over the 12 edges e=(p,q) of the cell with an interior end point of
+//   -h_a^-2 (lambda_p - lambda_q)(phi_p - phi_q) * dk_e/dln k_c,
+//   dk_e/dln k_c = k_e^2/(4 k_c) (harmonic edge mean) or k_c/4 (arithmetic).
+__global__ void k_gradient(const double* __restrict__ kc, const double* __restrict__ phi,
+                           const double* __restrict__ lam, Geom g, double ihx2, double ihy2, double ihz2,
+                           int face_rule, double* __restrict__ grad) {
+  const int cx = g.nx + 1, cy = g.ny + 1, cz = g.nz + 1;
+  const i64 n = (i64)cx * cy * cz;
+  auto cell = [&](int a, int b, int c) { return kc[((i64)c * cy + b) * cx + a]; };
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int ci = (int)(t % cx);
+    const i64 r = t / cx;
+    const int cj = (int)(r % cy);
+    const int ck = (int)(r / cy);
+    const double kcv = kc[t];
+    double acc = 0.0;
+    // corner (a,b,c) of the cell is interior point (ci-1+a, cj-1+b, ck-1+c)
+    auto node = [&](const double* v, int a, int b, int c) { return v[g.at(ci - 1 + a, cj - 1 + b, ck - 1 + c)]; };
+    auto add = [&](double ke, double ih2, int a0, int b0, int c0, int a1, int b1, int c1) {
+      const double dl = node(lam, a0, b0, c0) - node(lam, a1, b1, c1);
+      const double dp = node(phi, a0, b0, c0) - node(phi, a1, b1, c1);
+      const double dke = face_rule ? 0.25 * kcv : ke * ke / (4.0 * kcv);
+      acc += -ih2 * dl * dp * dke;
+    };
+    for (int v = 0; v < 2; ++v)
+      for (int u = 0; u < 2; ++u) {
+        {  // x-edge at (J, K) = (cj+u, ck+v): needs J, K interior (full coordinates)
+          const int J = cj + u, K = ck + v;
+          if (J >= 1 && J <= g.ny && K >= 1 && K <= g.nz) {
+            const double ke = edge_mean(cell(ci, J - 1, K - 1), cell(ci, J, K - 1), cell(ci, J - 1, K),
+                                        cell(ci, J, K), face_rule);
+            add(ke, ihx2, 0, u, v, 1, u, v);
+          }
+        }
+        {  // y-edge at (I, K) = (ci+u, ck+v)
+          const int I = ci + u, K = ck + v;
+          if (I >= 1 && I <= g.nx && K >= 1 && K <= g.nz) {
+            const double ke = edge_mean(cell(I - 1, cj, K - 1), cell(I, cj, K - 1), cell(I - 1, cj, K),
+                                        cell(I, cj, K), face_rule);
+            add(ke, ihy2, u, 0, v, u, 1, v);
+          }
+        }
+        {  // z-edge at (I, J) = (ci+u, cj+v)
+          const int I = ci + u, J = cj + v;
+          if (I >= 1 && I <= g.nx && J >= 1 && J <= g.ny) {
+            const double ke = edge_mean(cell(I - 1, J - 1, ck), cell(I, J - 1, ck), cell(I - 1, J, ck),
+                                        cell(I, J, ck), face_rule);
+            add(ke, ihz2, u, v, 0, u, v, 1);
+          }
+        }
+      }
+    grad[t] = acc;
+  }
+}
+
+// ------------------------------------------------------------ telescoped bottom
+// The coarse end of the hierarchy runs inside one thread block: levels
+// lb..L-1 of the V-cycle (pre-smooth, residual, restriction down; dense
+// Cholesky solve on the coarsest level; prolongation and post-smooth up), with
+// __syncthreads() between the per-level passes instead of kernel launches.
+constexpr int BOT_MAX = 8;
+constexpr int BOT_THREADS = 1024;
+
+template <class TV, class TC> struct BotLevel {
+  Geom g;
+  TV* x[2];
+  TV* d;
+  TV* b;
+  TV* r;
+  const TV* dinv;
+  const TC *kx, *ky, *kz;
+};
+
+template <class TV, class TC> struct BotArgs {
+  BotLevel<TV, TC> lv[BOT_MAX];
+  int nlev;            // levels in this kernel; the last one is the coarsest
+  int nu_pre, nu_post, degree;
+  double theta, delta, sigma;
+  const double* Lc;    // Cholesky factor of the coarsest operator (n x n)
+  int nc;
+};
+
+template <class R, class TV, class TC>
+__device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const BotArgs<TV, TC>& a) {
+  const R inv_theta = (R)(1.0 / a.theta);
+  double rho_prev = 1.0 / a.sigma;
+  int j0 = 0;
+  if (zero) {
+    if (a.degree == 1) {
+      OpChebZero1<R, TV> op{L.b, L.dinv, L.x[cur ^ 1], inv_theta};
+      block_for(op, L.g);
+      __syncthreads();
+      return cur ^ 1;
+    }
+    const double rho = 1.0 / (2.0 * a.sigma - rho_prev);
+    OpChebZero<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], a.degree > 2 ? L.d : nullptr, L.kx, L.ky, L.kz,
+                             (R)(rho * rho_prev), (R)(2.0 * rho / a.delta), inv_theta};
+    block_for(op, L.g);
+    __syncthreads();
+    cur ^= 1;
+    rho_prev = rho;
+    j0 = 2;
+  }
+  for (int j = j0; j < a.degree; ++j) {
+    double c1 = 0.0, c2 = 0.0;
+    if (j > 0) {
+      const double rho = 1.0 / (2.0 * a.sigma - rho_prev);
+      c1 = rho * rho_prev;
+      c2 = 2.0 * rho / a.delta;
+      rho_prev = rho;
+    }
+    OpChebStep<R, TV, TC> op{L.x[cur], j > 0 ? L.d : nullptr, L.b, L.dinv, L.x[cur ^ 1],
+                             j + 1 < a.degree ? L.d : nullptr, L.kx, L.ky, L.kz, (R)c1, (R)c2, inv_theta};
+    block_for(op, L.g);
+    __syncthreads();
+    cur ^= 1;
+  }
+  return cur;
+}
+
+// Coarsest solve x = L^-T L^-1 b in float64.  n <= 32: one warp with shuffles;
+// otherwise the whole block with shared-memory substitution.
+template <class TV>
+__device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, int n) {
+  __shared__ double y[1024];
+  for (int u = threadIdx.x; u < n; u += blockDim.x) {
+    const int i = u % g.nx, j = (u / g.nx) % g.ny, k = u / (g.nx * g.ny);
+    y[u] = cvt<double>(b[g.at(i, j, k)]);
+  }
+  __syncthreads();
+  if (n <= 32) {
+    if (threadIdx.x < 32) {
+      const int l = threadIdx.x;
+      double v = l < n ? y[l] : 0.0;
+      for (int c = 0; c < n; ++c) {  // forward: L y = b
+        const double yc = __shfl_sync(0xffffffffu, v, c) / Lc[(i64)c * n + c];
+        if (l == c) v = yc;
+        if (l > c && l < n) v -= Lc[(i64)l * n + c] * yc;
+      }
+      for (int c = n - 1; c >= 0; --c) {  // backward: L^T x = y
+        const double xc = __shfl_sync(0xffffffffu, v, c) / Lc[(i64)c * n + c];
+        if (l == c) v = xc;
+        if (l < c) v -= Lc[(i64)c * n + l] * xc;
+      }
+      if (l < n) y[l] = v;
+    }
+  } else {
+    for (int c = 0; c < n; ++c) {
+      if (threadIdx.x == 0) y[c] /= Lc[(i64)c * n + c];
+      __syncthreads();
+      for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) y[i] -= Lc[(i64)i * n + c] * y[c];
+      __syncthreads();
+    }
+    for (int c = n - 1; c >= 0; --c) {
+      if (threadIdx.x == 0) y[c] /= Lc[(i64)c * n + c];
+      __syncthreads();
+      for (int i = threadIdx.x; i < c; i += blockDim.x) y[i] -= Lc[(i64)c * n + i] * y[c];
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < n; u += blockDim.x) {
+    const int i = u % g.nx, j = (u / g.nx) % g.ny, k = u / (g.nx * g.ny);
+    x[g.at(i, j, k)] = store_as<TV>(y[u]);
+  }
+  __syncthreads();
+}
+
+// out_cur[0] receives the buffer index holding the result on the first level.
+template <class R, class TV, class TC>
+__global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> a) {
+  int cur[BOT_MAX];
+  const int L = a.nlev;
+  for (int l = 0; l < L - 1; ++l) {
+    const BotLevel<TV, TC>& V = a.lv[l];
+    cur[l] = 0;
+    for (int s = 0; s < a.nu_pre; ++s) cur[l] = bot_sweep<R>(V, cur[l], s == 0, a);
+    if (a.nu_pre == 0) {
+      for (i64 t = threadIdx.x; t < V.g.len; t += blockDim.x) V.x[0][t] = store_as<TV>(0.0);
+      __syncthreads();
+    }
+    double dummy = 0.0, d2 = 0.0;
+    (void)dummy;
+    (void)d2;
+    OpResidual<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.kx, V.ky, V.kz};
+    block_for(res, V.g);
+    __syncthreads();
+    OpRestrict<R, TV> rs{V.g, V.r, a.lv[l + 1].b};
+    block_for(rs, a.lv[l + 1].g);
+    __syncthreads();
+  }
+  bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.nc);
+  cur[L - 1] = 0;
+  for (int l = L - 2; l >= 0; --l) {
+    const BotLevel<TV, TC>& V = a.lv[l];
+    OpProlong<R, TV> pr{a.lv[l + 1].g, a.lv[l + 1].x[cur[l + 1]], V.x[cur[l]]};
+    block_for(pr, V.g);
+    __syncthreads();
+    for (int s = 0; s < a.nu_post; ++s) cur[l] = bot_sweep<R>(V, cur[l], false, a);
+  }
+}
+
+}  // namespace mgdev

@@ -1,0 +1,327 @@
+"""GPU parity: every step of the hot path, through the C ABI, against the CPU
+FP64 oracle on the same seeded inputs.
+
+Tolerances (float64 path): one operator application, smoother step,
+restriction or prolongation differs from the oracle only by rounding order and
+fused multiply-adds, a few ulp of the largest term: 1e-13 relative to the
+largest output magnitude.  A V-cycle chains a few dozen such steps: 1e-12.
+Full solves: relative 2-norm 1e-10 with the iteration count within 1.
+"""
+import numpy as np
+import pytest
+import torch
+
+import mg_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def N(t):
+    return t.detach().cpu().numpy()
+
+
+def relmax(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def rel2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = [
+    # (dims (Nz, Ny, Nx), block, log10 k range, params)
+    ((33, 33, 33), 8, 1.0, {}),
+    ((17, 9, 33), 4, 2.0, {}),
+    ((33, 17, 65), 4, 2.0, dict(face_rule=1, coarse_k_rule=1)),
+    ((17, 17, 17), 2, 3.0, dict(cheby_degree=3, nu_pre=2, nu_post=2, coarse_k_rule=2)),
+    ((9, 17, 9), 2, 1.0, dict(cheby_degree=1)),
+]
+
+
+def make(dims, block, rng, params, seed=101):
+    import paper_1604_07163_gb300 as mg
+    k = mi.cell_k(dims, block, -rng, rng, seed)
+    op = {kk: v for kk, v in params.items() if kk in ("face_rule", "coarse_k_rule", "cheby_degree", "nu_pre", "nu_post")}
+    O = oracle.Oracle(k, degree=op.get("cheby_degree", 2), nu_pre=op.get("nu_pre", 1), nu_post=op.get("nu_post", 1),
+                      coarse_rule=op.get("coarse_k_rule", 0), face_rule=op.get("face_rule", 0))
+    S = mg.MGSolver(T(k), mg.Params(**params))
+    assert S.num_levels == O.levels
+    return k, O, S
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_step_parity_fp64(gpu_lib, case):
+    dims, block, rng, params = CASES[case]
+    k, O, S = make(dims, block, rng, params)
+    for l in range(O.levels):
+        d = O.level_dims(l)
+        assert S.level_shape(l) == d
+        x = mi.random_nodal(d, 10 + l)
+        b = mi.random_nodal(d, 20 + l)
+        assert relmax(N(S.apply(T(x), l)), O.apply(x, l)) < 1e-13, ("apply", l)
+        if l < O.levels - 1:
+            assert relmax(N(S.smooth(T(b), None, l)), O.smooth(b, None, l)) < 1e-13, ("smooth0", l)
+            assert relmax(N(S.smooth(T(b), T(x), l)), O.smooth(b, x, l)) < 1e-13, ("smooth", l)
+            assert relmax(N(S.residual_restrict(T(b), T(x), l)), O.residual_restrict(b, x, l)) < 1e-13, ("rr", l)
+            e = mi.random_nodal(O.level_dims(l + 1), 30 + l)
+            assert relmax(N(S.prolong_add(T(e), T(x), l)), O.prolong_add(e, x, l)) < 1e-13, ("prolong", l)
+    bc = mi.random_nodal(O.level_dims(O.levels - 1), 40)
+    assert relmax(N(S.coarse_solve(T(bc))), O.coarse_solve(bc)) < 1e-12
+    r = mi.random_nodal(dims, 50)
+    assert relmax(N(S.vcycle(T(r))), O.vcycle(r)) < 1e-12
+    # the float64 outer operator
+    x = mi.random_nodal(dims, 60)
+    assert relmax(N(S.apply(T(x), -1)), O.apply(x)) < 1e-13
+
+
+def test_boundary_entries_ignored_and_zeroed(gpu_lib):
+    dims = (17, 17, 17)
+    k, O, S = make(dims, 4, 1.0, {})
+    x = mi.random_nodal(dims, 1)
+    junk = x.copy()
+    junk[0] = 7.0
+    junk[:, :, -1] = -3.0
+    y = N(S.apply(T(junk)))
+    assert np.all(y[0] == 0) and np.all(y[:, :, -1] == 0)
+    assert relmax(y, O.apply(x)) < 1e-13
+
+
+def test_gradient_kernel_parity(gpu_lib):
+    for face_rule in (0, 1):
+        dims = (17, 9, 33)
+        k, O, S = make(dims, 2, 2.0, dict(face_rule=face_rule))
+        phi = mi.random_nodal(dims, 3)
+        lam = mi.random_nodal(dims, 4)
+        assert relmax(N(S.gradient(T(phi), T(lam))), O.gradient(phi, lam)) < 1e-13
+
+
+@pytest.mark.parametrize("name,n,tol", [("poisson33_fp64", None, 1e-10), ("adjoint129", None, 1e-10),
+                                        ("poisson257_c1e4", 65, 2e-9)])
+def test_solve_parity_fp64(gpu_lib, name, n, tol):
+    """The two FP64 runs differ only in rounding order (tree vs sequential dot
+    products, fused multiply-adds).  CG amplifies that difference with the
+    condition number: at 10^2 contrast (33^3, 129^3) the solutions agree to
+    1e-10; at 10^4 contrast the amplification reaches a few 1e-10 after ~35
+    iterations, so that case is held to 2e-9, a fifth of its solve tolerance."""
+    dims, k, f, spec = mi.workload(name, n)
+    O = oracle.Oracle(k)
+    xo, ito, info = O.pcg(f, spec["rtol"], maxit=2000)
+    import paper_1604_07163_gb300 as mg
+    S = mg.MGSolver(T(k), mg.Params(maxit=2000))
+    x, st = S.solve(T(f), spec["rtol"])
+    assert abs(st.iters - ito) <= 1, (st.iters, ito)
+    assert st.true_rel_resid <= spec["rtol"] * 1.01
+    xg = N(x)
+    if st.iters == ito:
+        assert rel2(xg, xo) <= tol
+    else:  # same number of iterations on the oracle side
+        xo2, _, _ = O.pcg(f, 0.0, maxit=st.iters)
+        assert rel2(xg, xo2) <= tol
+    # recurrence-residual history agrees iteration by iteration
+    h = np.array(st.history)
+    m = min(len(h), len(info["hist"]))
+    assert np.max(np.abs(h[:m] - info["hist"][:m]) / info["hist"][:m]) < 1e-6
+
+
+def test_fixed_iteration_parity_and_not_converged(gpu_lib):
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    O = oracle.Oracle(k)
+    import paper_1604_07163_gb300 as mg
+    S = mg.MGSolver(T(k), mg.Params(maxit=5))
+    x, st = S.solve(T(f), 1e-30, raise_on_error=False)
+    assert st.status == "MG_ERR_NOT_CONVERGED" and st.iters == 5
+    xo, ito, _ = O.pcg(f, 1e-30, maxit=5)
+    assert ito == 5
+    assert rel2(N(x), xo) < 1e-12
+
+
+def test_flexible_cg_parity(gpu_lib):
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    O = oracle.Oracle(k)
+    xo, ito, _ = O.pcg(f, 1e-10, flexible=True)
+    import paper_1604_07163_gb300 as mg
+    x, st = mg.MGSolver(T(k), mg.Params(flexible=1)).solve(T(f), 1e-10)
+    assert abs(st.iters - ito) <= 1 and rel2(N(x), xo) < 1e-10
+
+
+def test_telescoping_and_graph_do_not_change_the_result(gpu_lib):
+    """Running coarse levels on fewer blocks (down to one block) or replaying
+    the V-cycle from a CUDA graph leaves every point operation unchanged."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64", 65)
+    ref = None
+    for tele, graph in [(0, 0), (4096, 1), (40000, 1), (10 ** 6, 0)]:
+        x, st = mg.MGSolver(T(k), mg.Params(telescope_max_n=tele, use_graph=graph)).solve(T(f), 1e-10)
+        if ref is None:
+            ref = (N(x), st.iters)
+        else:
+            assert st.iters == ref[1]
+            assert rel2(N(x), ref[0]) < 1e-13
+
+
+def test_repeated_solves_bitwise_identical(gpu_lib):
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64", 65)
+    S = mg.MGSolver(T(k))
+    a, s1 = S.solve(T(f), 1e-10)
+    b, s2 = S.solve(T(f), 1e-10)
+    assert s1.iters == s2.iters and torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["mixed_fp32", "mixed_bf16k"])
+def test_mixed_precision_reaches_fp64_tolerance(gpu_lib, precision):
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    O = oracle.Oracle(k)
+    xo, ito, _ = O.pcg(f, 1e-12)
+    x, st = mg.MGSolver(T(k), mg.Params(precision=precision)).solve(T(f), 1e-10)
+    assert st.true_rel_resid <= 1.05e-10
+    assert rel2(N(x), xo) < 1e-8
+    assert st.iters <= ito + 6
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed_fp32", 2e-6), ("mixed_bf16k", 2e-2)])
+def test_mixed_step_parity(gpu_lib, precision, tol):
+    """float32 vectors: rounding of order 1e-7 relative per step; bfloat16
+    coefficients perturb each edge by up to 2^-9 relative."""
+    dims = (33, 17, 33)
+    k, O, S = make(dims, 4, 1.0, dict(precision=precision))
+    for l in range(O.levels - 1):
+        d = O.level_dims(l)
+        x = mi.random_nodal(d, 10 + l)
+        b = mi.random_nodal(d, 20 + l)
+        assert relmax(N(S.apply(T(x), l)), O.apply(x, l)) < tol
+        assert relmax(N(S.smooth(T(b), T(x), l)), O.smooth(b, x, l)) < tol
+        assert relmax(N(S.residual_restrict(T(b), T(x), l)), O.residual_restrict(b, x, l)) < tol
+        e = mi.random_nodal(O.level_dims(l + 1), 30 + l)
+        assert relmax(N(S.prolong_add(T(e), T(x), l)), O.prolong_add(e, x, l)) < 2e-6
+    x = mi.random_nodal(dims, 60)
+    assert relmax(N(S.apply(T(x), -1)), O.apply(x)) < 1e-13
+
+
+# ------------------------------------------------------------------ edge cases
+def test_zero_rhs(gpu_lib):
+    import paper_1604_07163_gb300 as mg
+    dims = (9, 9, 9)
+    S = mg.MGSolver(T(np.ones((8, 8, 8))))
+    x, st = S.solve(torch.zeros(dims, dtype=torch.float64, device=DEV), 1e-8)
+    assert st.iters == 0 and torch.count_nonzero(x) == 0
+
+
+def test_nonfinite_and_invalid_inputs(gpu_lib):
+    import paper_1604_07163_gb300 as mg
+    dims = (9, 9, 9)
+    S = mg.MGSolver(T(np.ones((8, 8, 8))))
+    f = mi.rhs_f(dims, 1)
+    f[4, 4, 4] = np.nan
+    with pytest.raises(mg.MgError) as e:
+        S.solve(T(f), 1e-8)
+    assert e.value.status == "MG_ERR_NONFINITE"
+    k = np.ones((8, 8, 8))
+    k[1, 2, 3] = 0.0
+    with pytest.raises(mg.MgError) as e:
+        mg.MGSolver(T(k))
+    assert e.value.status == "MG_ERR_NONFINITE"
+    with pytest.raises(mg.MgError) as e:
+        mg.MGSolver(T(np.ones((9, 8, 8))), mg.Params(levels=3))  # 10 vertices: 9 not divisible by 4
+    assert e.value.status == "MG_ERR_ARG"
+    with pytest.raises(mg.MgError) as e:
+        mg.MGSolver(T(np.ones((32, 32, 32))), mg.Params(levels=1))  # 31^3 unknowns > dense limit
+    assert e.value.status == "MG_ERR_ARG"
+
+
+def test_single_level_is_a_direct_solve(gpu_lib):
+    import paper_1604_07163_gb300 as mg
+    dims = (9, 9, 9)
+    k = mi.cell_k(dims, 2, -2, 2, 5)
+    f = mi.rhs_f(dims, 5)
+    O = oracle.Oracle(k, levels=1)
+    xo, _, _ = O.pcg(f, 1e-14)
+    x, st = mg.MGSolver(T(k), mg.Params(levels=1)).solve(T(f), 1e-12)
+    assert st.iters == 1 and rel2(N(x), xo) < 1e-12
+
+
+def test_nonzero_initial_guess(gpu_lib):
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    O = oracle.Oracle(k)
+    x0 = mi.random_nodal(dims, 77)
+    xo, ito, _ = O.pcg(f, 1e-10, x0=x0)
+    x, st = mg.MGSolver(T(k), mg.Params(nonzero_guess=1)).solve(T(f), 1e-10, x=T(x0))
+    assert abs(st.iters - ito) <= 1 and rel2(N(x), xo) < 1e-10
+    # warm start from the converged answer: no iteration needed
+    x2, st2 = mg.MGSolver(T(k), mg.Params(nonzero_guess=1)).solve(T(f), 1e-8, x=x.clone())
+    assert st2.iters == 0
+
+
+def test_residual_norm_entry_point(gpu_lib):
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    O = oracle.Oracle(k)
+    x = mi.random_nodal(dims, 8)
+    S = mg.MGSolver(T(k))
+    got = S.residual_norm(T(f), T(x))
+    want = np.linalg.norm(f - O.apply(x))
+    assert abs(got - want) <= 1e-12 * want
+
+
+# ------------------------------------------------------------------ adjoint
+def test_adjoint_gradient_parity_129(gpu_lib):
+    """Gradient of L = 0.5 sum_mask (phi - phi_obs)^2 on the 129^3 workload:
+    GPU adjoint vs the oracle's gradient from the oracle's own solves."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("adjoint129")
+    kobs = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], spec["seed"] + 1)
+    phi_obs, _, _ = oracle.Oracle(kobs).pcg(f, 1e-12)
+    mask = mi.obs_mask(dims, spec["seed"])
+    O = oracle.Oracle(k)
+    phi_o, _, _ = O.pcg(f, 1e-12)
+    g_o = np.where(mask, phi_o - phi_obs, 0.0)
+    lam_o, _, _ = O.pcg(g_o, 1e-12)
+    grad_o = O.gradient(phi_o, lam_o)
+
+    logk = T(np.log(k)).requires_grad_(True)
+    ft = T(f).requires_grad_(True)
+    phi = mg.mg_solve(ft, logk, rtol=1e-12)
+    loss = 0.5 * ((phi - T(phi_obs)) ** 2 * T(mask.astype(np.float64))).sum()
+    loss.backward()
+    assert rel2(N(phi), phi_o) < 1e-10
+    assert rel2(N(ft.grad), lam_o) < 1e-9
+    assert rel2(N(logk.grad), grad_o) < 1e-8
+
+
+def test_gradient_finite_differences_gpu(gpu_lib):
+    """Central differences (h = 1e-6, forward solves to 1e-13) on 32 seeded cells."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("adjoint129", 33)
+    kobs = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], spec["seed"] + 1)
+    phi_obs = T(oracle.Oracle(kobs).pcg(f, 1e-13)[0])
+    mask = T(mi.obs_mask(dims, spec["seed"], frac=0.2).astype(np.float64))
+    ft = T(f)
+    lk = np.log(k)
+
+    def loss(lkv, grad=False):
+        logk = T(lkv).requires_grad_(grad)
+        phi = mg.mg_solve(ft, logk, rtol=1e-13)
+        Lv = 0.5 * ((phi - phi_obs) ** 2 * mask).sum()
+        if grad:
+            Lv.backward()
+            return Lv.item(), N(logk.grad)
+        return Lv.item()
+
+    L0, g = loss(lk, True)
+    rng = np.random.default_rng(5)
+    cells = [tuple(c) for c in rng.integers(0, 32, (32, 3))]
+    h = 1e-6
+    for c in cells:
+        lp = lk.copy(); lp[c] += h
+        lm = lk.copy(); lm[c] -= h
+        fd = (loss(lp) - loss(lm)) / (2 * h)
+        assert abs(fd - g[c]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(g).max()), (c, fd, g[c])
