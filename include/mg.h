@@ -164,6 +164,31 @@ mg_status mg_gradient(mg_handle* h, const double* phi, const double* lambda, dou
 /* ||f - A x||_2 on the float64 finest operator, written to *out (host). */
 mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, double* out);
 
+/* ---- residual norm without any device allocation --------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory at the time they check a solution:
+ * code running where another memory manager owns the whole device (so a raw
+ * cudaMalloc would fail or fragment its pool), or code that must keep a fixed
+ * memory footprint.  It computes ||f - A x||_2 over interior nodes with the
+ * handle's float64 finest operator, like mg_residual_norm, but reads f and x
+ * in their dense nodal layout directly (no copy into the handle's buffers),
+ * keeps its per-plane partial sums in a statically sized device array that
+ * the library holds for the life of the process, and writes the result to
+ * the DEVICE pointer out (one double) without synchronising.
+ *  - f, x: device nodal arrays of the handle's finest grid (boundary entries
+ *    ignored).  out: device pointer to one double.  All owned by the caller.
+ *  - Allocates nothing: no cudaMalloc/cudaFree, no allocating library call.
+ *  - Limit: Nz - 2 (interior planes) <= MG_NOALLOC_MAX_PLANES; larger grids
+ *    are rejected with MG_ERR_ARG.
+ *  - The first call on each device looks up the address of the static array
+ *    with that device current; make that first call before any stream
+ *    capture.
+ *  - Every call shares the one static array (per device): calls that overlap
+ *    on the GPU (different streams or handles at the same time) race.  Each
+ *    call writes every partial it later reads, so no clearing is needed. */
+#define MG_NOALLOC_MAX_PLANES 4096
+mg_status mg_residual_norm_noalloc(mg_handle* h, const double* f, const double* x, double* out);
+
 /* ---- kernel timing (opt-in, for benchmarks; not part of the method) ------
  * When enabled, every kernel launch of the solve is bracketed by CUDA events
  * on the launching stream and its device time is accumulated per kernel class

@@ -19,7 +19,7 @@ EXPORTS = [
     "mg_params_default", "mg_setup", "mg_set_stream", "mg_solve", "mg_solve_adjoint", "mg_free", "mg_last_error",
     "mg_num_levels", "mg_level_dims", "mg_history", "mg_apply", "mg_smooth", "mg_residual_restrict",
     "mg_prolong_add", "mg_coarse_solve", "mg_vcycle", "mg_gradient", "mg_residual_norm", "mg_timing_enable",
-    "mg_timing_read",
+    "mg_timing_read", "mg_residual_norm_noalloc",
 ]
 KERNEL_CLASSES = ["cheb_zero", "cheb_step", "resid", "restrict", "prolong", "bottom", "cg_dir", "cg_upd", "dot",
                   "cast", "cg_apply"]
@@ -82,6 +82,7 @@ def load():
         "mg_gradient": ([vp, vp, vp, vp], i),
         "mg_residual_norm": ([vp, vp, vp, P(C.c_double)], i),
         "mg_timing_enable": ([vp, i], i),
+        "mg_residual_norm_noalloc": ([vp, vp, vp, vp], i),
         "mg_timing_read": ([vp, i, i, P(C.c_double), P(C.c_longlong), P(C.c_double)], i),
     }
     for name, (args, res) in sig.items():

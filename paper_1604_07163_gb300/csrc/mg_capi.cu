@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -960,6 +961,92 @@ mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, doubl
   finish(h, nb, FIN_TRUE);
   if ((s = read_scal(h)) != MG_OK) return s;
   *out = std::sqrt(h->hsc->true_rr);
+  return MG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Residual norm for callers that cannot allocate: per-plane partial sums live
+// in this file-scope device array instead of the handle's scratch buffers.
+namespace {
+
+static __device__ __align__(256) double g_noalloc_partials[MG_NOALLOC_MAX_PLANES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_partials on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// One block per interior plane k: sum over the plane of (f - A x)^2 with f and
+// x in the dense full-grid layout (boundary entries treated as zero) and the
+// float64 operator read from the handle's padded coefficient arrays.
+__global__ void __launch_bounds__(256) k_resnorm_planes(const double* __restrict__ f, const double* __restrict__ x,
+                                                        const double* __restrict__ kx, const double* __restrict__ ky,
+                                                        const double* __restrict__ kz, const double* __restrict__ dg,
+                                                        Geom g, double* partials) {
+  const int k = blockIdx.x;
+  const int Nx = g.nx + 2, Ny = g.ny + 2, Nz = g.nz + 2;
+  const i64 sy = Nx, sz = (i64)Nx * Ny;
+  auto X = [&](int I, int J, int K) -> double {
+    const bool in = I >= 1 && I <= Nx - 2 && J >= 1 && J <= Ny - 2 && K >= 1 && K <= Nz - 2;
+    return in ? x[(i64)K * sz + (i64)J * sy + I] : 0.0;
+  };
+  double acc = 0.0, unused = 0.0;
+  const int n = g.nx * g.ny;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = t % g.nx, j = t / g.nx;
+    const int I = i + 1, J = j + 1, K = k + 1;
+    const i64 p = g.at(i, j, k);
+    const double S = kx[p - 1] * X(I - 1, J, K) + kx[p] * X(I + 1, J, K) + ky[p - g.Px] * X(I, J - 1, K) +
+                     ky[p] * X(I, J + 1, K) + kz[p - g.sz] * X(I, J, K - 1) + kz[p] * X(I, J, K + 1);
+    const double r = f[(i64)K * sz + (i64)J * sy + I] - (dg[p] * X(I, J, K) - S);
+    acc = fma(r, r, acc);
+  }
+  block_sum2<256>(acc, unused);
+  if (threadIdx.x == 0) partials[k] = acc;
+}
+
+// Sum of the per-plane partials in plane order; out = sqrt(sum).
+__global__ void __launch_bounds__(256) k_resnorm_sum(const double* partials, int n, double* out) {
+  double a = 0.0, unused = 0.0;
+  for (int t = threadIdx.x; t < n; t += 256) a += partials[t];
+  block_sum2<256>(a, unused);
+  if (threadIdx.x == 0) out[0] = sqrt(a);
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_residual_norm_noalloc(mg_handle* h, const double* f, const double* x, double* out) {
+  if (!h || !f || !x || !out) return h ? fail(h, MG_ERR_ARG, "null pointer") : MG_ERR_ARG;
+  const LevelBuf& L0 = h->lv[0];
+  if (L0.g.nz > MG_NOALLOC_MAX_PLANES)
+    return fail(h, MG_ERR_ARG, "mg_residual_norm_noalloc: grid has more than MG_NOALLOC_MAX_PLANES interior planes");
+  double* scratch = nullptr;
+  CK(noalloc_scratch(&scratch));
+  Guard guard(h);
+  k_resnorm_planes<<<L0.g.nz, 256, 0, h->s>>>(f, x, L0.kx64, L0.ky64, L0.kz64, h->dg64, L0.g, scratch);
+  k_resnorm_sum<<<1, 256, 0, h->s>>>(scratch, L0.g.nz, out);
+  CKL();
   return MG_OK;
 }
 
