@@ -79,6 +79,10 @@ typedef struct {
   int flexible;        /* CG beta: 0 Fletcher-Reeves, 1 Polak-Ribiere (flexible); -1 = 0 for FP64, 1 for mixed */
   int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
   int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
+  int stencil_kernel;  /* smoother/residual kernels: 0 automatic (currently the z-marching kernels, the
+                          faster of the two on GB300 as measured), 1 register/L1 z-marching everywhere,
+                          2 TMA-staged tiles wherever a level is not in the single-block bottom */
+  int use_pdl;         /* 1: launch solve kernels as programmatic dependent launches (default 1) */
 } mg_params;
 
 typedef struct {
@@ -190,10 +194,12 @@ mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, doubl
 mg_status mg_residual_norm_noalloc(mg_handle* h, const double* f, const double* x, double* out);
 
 /* ---- kernel timing (opt-in, for benchmarks; not part of the method) ------
- * When enabled, every kernel launch of the solve is bracketed by CUDA events
- * on the launching stream and its device time is accumulated per kernel class
- * and level.  Enabling or disabling resets the counters (and recaptures the
- * V-cycle graph on next use). */
+ * When enabled, every launch of a kernel class in class_mask (bit c = class c)
+ * on a level in level_mask (bit l = level l) is bracketed by CUDA events on
+ * the launching stream and its device time is accumulated per class and
+ * level.  class_mask = 0 disables timing.  While timing is on the V-cycle is
+ * launched kernel by kernel (not from the graph) so that the events are plain
+ * stream events.  Enabling or disabling resets the counters. */
 typedef enum {
   MG_K_CHEB_ZERO = 0,  /* smoother steps 0-1 from a zero guess (pre-smooth) */
   MG_K_CHEB_STEP = 1,  /* smoother step with a materialised iterate */
@@ -208,7 +214,7 @@ typedef enum {
   MG_K_CG_APPLY = 10,  /* q = A p, p.q with the float64 outer operator */
   MG_K_NCLASS = 11
 } mg_kernel_class;
-mg_status mg_timing_enable(mg_handle* h, int on);
+mg_status mg_timing_enable(mg_handle* h, int class_mask, int level_mask);
 /* Totals for class cls on level l (0 = finest): device milliseconds, number of
  * launches and interior points processed (summed over launches). */
 mg_status mg_timing_read(const mg_handle* h, int cls, int l, double* ms, long long* launches, double* points);

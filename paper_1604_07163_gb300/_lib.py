@@ -31,7 +31,7 @@ class MgParams(C.Structure):
         ("eig_lo_frac", C.c_double), ("eig_hi", C.c_double),
         ("coarse_k_rule", C.c_int), ("face_rule", C.c_int), ("k_is_log", C.c_int), ("precision", C.c_int),
         ("maxit", C.c_int), ("nonzero_guess", C.c_int), ("flexible", C.c_int), ("telescope_max_n", C.c_int),
-        ("use_graph", C.c_int),
+        ("use_graph", C.c_int), ("stencil_kernel", C.c_int), ("use_pdl", C.c_int),
     ]
 
 
@@ -81,7 +81,7 @@ def load():
         "mg_vcycle": ([vp, vp, vp], i),
         "mg_gradient": ([vp, vp, vp, vp], i),
         "mg_residual_norm": ([vp, vp, vp, P(C.c_double)], i),
-        "mg_timing_enable": ([vp, i], i),
+        "mg_timing_enable": ([vp, i, i], i),
         "mg_residual_norm_noalloc": ([vp, vp, vp, vp], i),
         "mg_timing_read": ([vp, i, i, P(C.c_double), P(C.c_longlong), P(C.c_double)], i),
     }

@@ -15,6 +15,7 @@
 
 #include "mg.h"
 #include "mg_kernels.cuh"
+#include "mg_tma.cuh"
 
 using namespace mgdev;
 
@@ -30,6 +31,10 @@ struct LevelBuf {
   void* dinv = nullptr;
   void* x[2] = {nullptr, nullptr};
   void *d = nullptr, *b = nullptr, *r = nullptr;
+  // TMA tensor maps (2-D row views) for the staged stencil kernels
+  bool tma = false;
+  CUtensorMap m_full_x[2], m_full_b, m_full_dinv, m_kx, m_ky, m_kz, m_c_dinv, m_c_b, m_c_d, m_c_r64;
+  int tma_grid[3] = {0, 0, 0}, tma_kchunk = 0;
 };
 
 std::string g_setup_error;
@@ -60,6 +65,9 @@ struct mg_handle {
   std::vector<void*> allocs;
   cudaGraphExec_t vexec = nullptr;
   int vexec_zcur = 0;
+  bool rz_fused = false;         // last V-cycle fused rho = r.z into its final step
+  int bot_smem_budget = 0;       // dynamic shared memory the bottom kernel may use
+  int lin_grid = 0;              // blocks of the linear (pointwise) kernels
   long long launches = 0;        // kernels launched (counted at launch sites)
   long long graph_launches = 0;  // kernels inside the captured V-cycle graph
   // opt-in kernel timing
@@ -69,6 +77,7 @@ struct mg_handle {
     int ev;  // index of the start event; ev + 1 is the stop event
   };
   bool timing = false;
+  int t_cls_mask = 0, t_lvl_mask = 0;
   bool capturing = false;
   std::vector<cudaEvent_t> evpool;
   int ev_graph_end = 0;  // events [0, ev_graph_end) belong to the captured graph
@@ -80,6 +89,21 @@ struct mg_handle {
 };
 
 namespace {
+
+template <class... KArgs, class... Args>
+void launch(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h->s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = h->prm.use_pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 using clk = std::chrono::steady_clock;
 double secs(clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); }
@@ -107,8 +131,10 @@ Geom make_geom(int nx, int ny, int nz) {
   g.Px = roundup(nx + 1, 8);
   g.Py = ny + 1;
   g.sz = (i64)g.Px * g.Py;
-  g.off = ((g.sz + g.Px + 1 + 31) / 32) * 32;
-  g.len = g.off + (i64)(nz + 1) * g.sz + 32;
+  // one pad plane and two pad rows in front (index (-1,-1,-1) = Px - 1 >= 0);
+  // off and len are multiples of Px so the arrays are 2-D tensors of rows
+  g.off = g.sz + 2 * (i64)g.Px;
+  g.len = g.off + (i64)(nz + 1) * g.sz + g.Px;
   return g;
 }
 
@@ -117,6 +143,11 @@ int lin_blocks(const mg_handle* h, i64 n) {
   i64 cap = (i64)h->nsm * 16;
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
+
+// Launch on the handle's stream, as a programmatic dependent launch when the
+// handle enables it (the kernel's first action is griddepcontrol.wait).
+template <class... KArgs, class... Args>
+void launch(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args);
 
 template <class T> mg_status alloc(mg_handle* h, T** p, i64 n) {
   void* q = nullptr;
@@ -139,11 +170,50 @@ template <class T> mg_status alloc(mg_handle* h, T** p, i64 n) {
     ptr = t_;                                          \
   } while (0)
 
+// ---- TMA tensor maps ---------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tma_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+template <class T> CUtensorMapDataType tma_dtype();
+template <> CUtensorMapDataType tma_dtype<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+template <> CUtensorMapDataType tma_dtype<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> CUtensorMapDataType tma_dtype<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+
+// 2-D view of a padded level array: rows of Px elements; box bw x bh elements.
+template <class T> bool tma_encode(CUtensorMap* m, const void* base, const Geom& g, int bw, int bh) {
+  EncodeTiledFn fn = tma_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)g.Px, (cuuint64_t)(g.len / g.Px)};
+  const cuuint64_t strides[1] = {(cuuint64_t)g.Px * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, tma_dtype<T>(), 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // ---- opt-in kernel timing: event pairs around launches, collected at sync points
 constexpr int EV_POOL = 2048;
 
-int tm_begin(mg_handle* h) {
+int tm_begin(mg_handle* h, int cls, int level) {
   if (!h->timing || h->ev_next + 2 > (int)h->evpool.size()) return -1;
+  if (!((h->t_cls_mask >> cls) & 1) || !((h->t_lvl_mask >> level) & 1)) return -1;
   const int e = h->ev_next;
   h->ev_next += 2;
   cudaEventRecordWithFlags(h->evpool[e], h->s, h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
@@ -192,16 +262,25 @@ template <bool RED, class Op>
 int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 0) {
   int kc;
   dim3 grid = zm_grid(h, g, &kc);
-  const int e = cls >= 0 ? tm_begin(h) : -1;
-  k_zmarch<Op, RED><<<grid, ZM_THREADS, 0, h->s>>>(op, g, kc, h->partials, h->pstride);
+  const int e = cls >= 0 ? tm_begin(h, cls, level) : -1;
+  launch(h, k_zmarch<Op, RED>, grid, dim3(ZM_THREADS), 0, op, g, kc, h->partials, h->pstride);
   ++h->launches;
   tm_end(h, e, cls, level, (double)g.npts());
   return grid.x * grid.y * grid.z;
 }
 
+template <bool RED, class Op> int linear(mg_handle* h, i64 n, const Op& op, int cls = -1) {
+  const int nb = h->lin_grid;
+  const int e = cls >= 0 ? tm_begin(h, cls, 0) : -1;
+  launch(h, k_linear<Op, RED>, dim3(nb), dim3(LIN_THREADS), 0, op, n, h->partials, h->pstride);
+  ++h->launches;
+  tm_end(h, e, cls, 0, (double)h->lv[0].g.npts());
+  return nb;
+}
+
 void finish(mg_handle* h, int nblocks, int mode) {
   int flex = h->prm.flexible;
-  k_finish<<<1, 256, 0, h->s>>>(h->partials, nblocks, h->pstride, mode, h->dsc, flex);
+  launch(h, k_finish, dim3(1), dim3(256), 0, (const double*)h->partials, nblocks, h->pstride, mode, h->dsc, flex);
   ++h->launches;
 }
 
@@ -228,8 +307,99 @@ template <class TV, class TC> struct Impl {
   static TV* V(void* p) { return (TV*)p; }
   static const TC* C(void* p) { return (const TC*)p; }
 
+  // ---- TMA-staged stencil launches -------------------------------------------
+  template <int KIND, bool HAS_D, bool DOT> static void tma_attr(mg_handle* h) {
+    using Lay = TmaLayout<KIND, HAS_D, DOT, TV, TC>;
+    cudaFuncSetAttribute(k_tma_stencil<KIND, HAS_D, DOT, TV, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Lay::SMEM);
+  }
+
+  // Encodes the tensor maps of level l and fixes its launch geometry.
+  static bool tma_prepare(mg_handle* h, int l) {
+    LevelBuf& Lv = h->lv[l];
+    const Geom& g = Lv.g;
+    constexpr int BWV = XHalo<TV>::BW, BWC = XHalo<TC>::BW;
+    bool ok = true;
+    for (int c = 0; c < 2; ++c) ok = ok && tma_encode<TV>(&Lv.m_full_x[c], Lv.x[c], g, BWV, TT_Y + 2);
+    ok = ok && tma_encode<TV>(&Lv.m_full_b, Lv.b, g, BWV, TT_Y + 2);
+    ok = ok && tma_encode<TV>(&Lv.m_full_dinv, Lv.dinv, g, BWV, TT_Y + 2);
+    ok = ok && tma_encode<TC>(&Lv.m_kx, Lv.kx, g, BWC, TT_Y);
+    ok = ok && tma_encode<TC>(&Lv.m_ky, Lv.ky, g, TT_X, TT_Y + 1);
+    ok = ok && tma_encode<TC>(&Lv.m_kz, Lv.kz, g, TT_X, TT_Y);
+    ok = ok && tma_encode<TV>(&Lv.m_c_dinv, Lv.dinv, g, TT_X, TT_Y);
+    ok = ok && tma_encode<TV>(&Lv.m_c_b, Lv.b, g, TT_X, TT_Y);
+    ok = ok && tma_encode<TV>(&Lv.m_c_d, Lv.d, g, TT_X, TT_Y);
+    if (l == 0) ok = ok && tma_encode<double>(&Lv.m_c_r64, h->cr, g, TT_X, TT_Y);
+    if (!ok) return false;
+    // grid: 32x8 tiles; planes split so that about one wave of blocks is
+    // resident (shared memory bounds the blocks per SM)
+    const int gx = (g.nx + TT_X - 1) / TT_X, gy = (g.ny + TT_Y - 1) / TT_Y;
+    tma_attr<TK_STEP, true, true>(h);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tma_stencil<TK_STEP, true, true, TV, TC>, TT_THREADS,
+                                                  TmaLayout<TK_STEP, true, true, TV, TC>::SMEM);
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    // whole waves only: the largest plane split whose blocks all fit at once
+    int zs = (h->nsm * per_sm) / (gx * gy);
+    zs = zs < 1 ? 1 : (zs > g.nz ? g.nz : zs);
+    const int kc = (g.nz + zs - 1) / zs;
+    Lv.tma_kchunk = kc;
+    Lv.tma_grid[0] = gx;
+    Lv.tma_grid[1] = gy;
+    Lv.tma_grid[2] = (g.nz + kc - 1) / kc;
+    tma_attr<TK_ZERO, false, false>(h);
+    tma_attr<TK_STEP, false, false>(h);
+    tma_attr<TK_STEP, true, false>(h);
+    tma_attr<TK_STEP, false, true>(h);
+    tma_attr<TK_STEP, true, true>(h);
+    tma_attr<TK_RESID, false, false>(h);
+    Lv.tma = true;
+    return true;
+  }
+
+  template <int KIND, bool HAS_D, bool DOT>
+  static int tma_launch(mg_handle* h, int l, const CUtensorMap& f0, const CUtensorMap* f1, TV* xout, TV* dout,
+                        double c1, double c2, double inv_theta, int cls) {
+    LevelBuf& Lv = h->lv[l];
+    TmaMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    maps.m[0] = f0;
+    if (f1) maps.m[1] = *f1;
+    maps.m[2] = Lv.m_kx;
+    maps.m[3] = Lv.m_ky;
+    maps.m[4] = Lv.m_kz;
+    maps.m[5] = Lv.m_c_dinv;
+    maps.m[6] = Lv.m_c_b;
+    maps.m[7] = Lv.m_c_d;
+    if (DOT) maps.m[8] = Lv.m_c_r64;
+    TmaArgs<TV, TC> a{};
+    a.g = Lv.g;
+    a.kchunk = Lv.tma_kchunk;
+    a.rowbase = (int)(Lv.g.off / Lv.g.Px);
+    a.xout = xout;
+    a.dout = dout;
+    a.kx = C(Lv.kx);
+    a.c1 = (float)c1;
+    a.c2 = (float)c2;
+    a.inv_theta = (float)inv_theta;
+    a.dc1 = c1;
+    a.dc2 = c2;
+    a.dinv_theta = inv_theta;
+    a.partials = h->partials;
+    a.status = &h->dsc->status;
+    using Lay = TmaLayout<KIND, HAS_D, DOT, TV, TC>;
+    dim3 grid(Lv.tma_grid[0], Lv.tma_grid[1], Lv.tma_grid[2]);
+    const int e = tm_begin(h, cls, l);
+    launch(h, k_tma_stencil<KIND, HAS_D, DOT, TV, TC>, grid, dim3(TT_THREADS), Lay::SMEM, maps, a);
+    ++h->launches;
+    tm_end(h, e, cls, l, (double)Lv.g.npts());
+    return grid.x * grid.y * grid.z;
+  }
+
   // One smoother sweep on level l starting from buffer cur; returns the new cur.
-  static int sweep(mg_handle* h, int l, int cur, bool zero) {
+  // With fuse_rz the last step also accumulates rho = r.z for the outer CG
+  // (finest level only) and finishes the CG scalars.
+  static int sweep(mg_handle* h, int l, int cur, bool zero, bool fuse_rz = false) {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
     double theta, delta, sigma;
@@ -244,10 +414,16 @@ template <class TV, class TC> struct Impl {
         return cur ^ 1;
       }
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
-      OpChebZero<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), p.cheby_degree > 2 ? V(Lv.d) : nullptr,
-                                C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(rho * rho_prev), (TV)(2.0 * rho / delta),
-                                inv_theta};
-      zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+      if (Lv.tma) {
+        tma_launch<TK_ZERO, false, false>(h, l, Lv.m_full_b, &Lv.m_full_dinv, V(Lv.x[cur ^ 1]),
+                                          p.cheby_degree > 2 ? V(Lv.d) : nullptr, rho * rho_prev, 2.0 * rho / delta,
+                                          1.0 / theta, MG_K_CHEB_ZERO);
+      } else {
+        OpChebZero<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), p.cheby_degree > 2 ? V(Lv.d) : nullptr,
+                                  C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(rho * rho_prev), (TV)(2.0 * rho / delta),
+                                  inv_theta};
+        zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+      }
       cur ^= 1;
       rho_prev = rho;
       j0 = 2;
@@ -263,10 +439,49 @@ template <class TV, class TC> struct Impl {
       OpChebStep<TV, TV, TC> op{V(Lv.x[cur]), j > 0 ? V(Lv.d) : nullptr, V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]),
                                 j + 1 < p.cheby_degree ? V(Lv.d) : nullptr, C(Lv.kx), C(Lv.ky), C(Lv.kz),
                                 (TV)c1, (TV)c2, inv_theta};
-      zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
+      const bool dot = fuse_rz && j + 1 == p.cheby_degree;
+      TV* xo = V(Lv.x[cur ^ 1]);
+      TV* dout = j + 1 < p.cheby_degree ? V(Lv.d) : nullptr;
+      if (Lv.tma) {
+        const CUtensorMap& f0 = Lv.m_full_x[cur];
+        int nb;
+        if (j > 0 && dot) nb = tma_launch<TK_STEP, true, true>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+        else if (j > 0) nb = tma_launch<TK_STEP, true, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+        else if (dot) nb = tma_launch<TK_STEP, false, true>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+        else nb = tma_launch<TK_STEP, false, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+        if (dot) {
+          finish(h, nb, FIN_RZ);
+          h->rz_fused = true;
+        }
+      } else if (dot) {
+        const int nb = zmarch<true>(h, Lv.g, OpChebStepDot<TV, TV, TC>{op, h->cr}, MG_K_CHEB_STEP, l);
+        finish(h, nb, FIN_RZ);
+        h->rz_fused = true;
+      } else {
+        zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
+      }
       cur ^= 1;
     }
     return cur;
+  }
+
+  // Shared-memory plan of the bottom kernel starting at level l0: arrays are
+  // placed greedily from the coarsest level up while they fit the budget.
+  static int bottom_smem_plan(const mg_handle* h, int l0, int soff[BOT_MAX][BA_N]) {
+    int used = 0;
+    for (int l = 0; l < BOT_MAX; ++l)
+      for (int q = 0; q < BA_N; ++q) soff[l][q] = -1;
+    for (int l = h->L - 1; l >= l0; --l) {
+      const i64 len = h->lv[l].g.len;
+      for (int q = 0; q < BA_N; ++q) {
+        const i64 nb = len * (i64)(q >= BA_KX ? sizeof(TC) : sizeof(TV));
+        if (used + nb <= h->bot_smem_budget) {
+          soff[l - l0][q] = used;
+          used += (int)((nb + 15) / 16 * 16);
+        }
+      }
+    }
+    return used;
   }
 
   static void bottom(mg_handle* h, int l0) {
@@ -292,15 +507,32 @@ template <class TV, class TC> struct Impl {
     cheb_consts(h->prm, &a.theta, &a.delta, &a.sigma);
     a.Lc = h->Lc;
     a.nc = h->nc;
-    const int e = tm_begin(h);
-    k_bottom<TV, TV, TC><<<1, BOT_THREADS, 0, h->s>>>(a);
+    a.result_cur = l0 == h->L - 1 ? 0 : level_result_cur(h->prm);
+    const int smem = bottom_smem_plan(h, l0, a.soff);
+    const int e = tm_begin(h, MG_K_BOTTOM, l0);
+    launch(h, k_bottom<TV, TV, TC>, dim3(1), dim3(BOT_THREADS), (size_t)smem, a);
     ++h->launches;
     tm_end(h, e, MG_K_BOTTOM, l0, (double)h->lv[l0].g.npts());
   }
 
+  // r = b - A x[cur] on level l, then b of level l+1 = R r.
+  static void residual_restrict(mg_handle* h, int l, int cur) {
+    LevelBuf& Lv = h->lv[l];
+    LevelBuf& Cv = h->lv[l + 1];
+    if (Lv.tma) {
+      tma_launch<TK_RESID, false, false>(h, l, Lv.m_full_x[cur], nullptr, V(Lv.r), nullptr, 0.0, 0.0, 0.0,
+                                         MG_K_RESID);
+    } else {
+      OpResidual<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)};
+      zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
+    }
+    OpRestrict<TV, TV> rs{Lv.g, V(Lv.r), V(Cv.b)};
+    zmarch<false>(h, Cv.g, rs, MG_K_RESTRICT, l);
+  }
+
   // V-cycle from level l with zero initial guess; b of level l must be set.
   // Returns the buffer index of level l holding the result.
-  static int vcycle(mg_handle* h, int l) {
+  static int vcycle(mg_handle* h, int l, bool fuse_rz = false) {
     if (l >= h->lb) {
       bottom(h, l);
       return l == h->L - 1 ? 0 : level_result_cur(h->prm);
@@ -310,30 +542,38 @@ template <class TV, class TC> struct Impl {
     int cur = 0;
     for (int s = 0; s < h->prm.nu_pre; ++s) cur = sweep(h, l, cur, s == 0);
     if (h->prm.nu_pre == 0) cudaMemsetAsync(Lv.x[0], 0, (size_t)Lv.g.len * sizeof(TV), h->s);
-    OpResidual<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)};
-    zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
-    OpRestrict<TV, TV> rs{Lv.g, V(Lv.r), V(Cv.b)};
-    zmarch<false>(h, Cv.g, rs, MG_K_RESTRICT, l);
+    residual_restrict(h, l, cur);
     const int ccur = vcycle(h, l + 1);
     OpProlong<TV, TV> pr{Cv.g, V(Cv.x[ccur]), V(Lv.x[cur])};
     zmarch<false>(h, Lv.g, pr, MG_K_PROLONG, l);
-    for (int s = 0; s < h->prm.nu_post; ++s) cur = sweep(h, l, cur, false);
+    for (int s = 0; s < h->prm.nu_post; ++s) cur = sweep(h, l, cur, false, fuse_rz && s + 1 == h->prm.nu_post);
     return cur;
   }
 
-  // z = M^-1 r on the float64 CG residual; returns the level-0 buffer (type TV)
+  // z = M^-1 r; the finest right-hand side (the float64 residual, or its
+  // float32 copy in the mixed forms) must be in place.  Ends with rho = r.z
+  // and the CG beta in the scalar block.  Returns the level-0 buffer (type TV)
   // holding z.
   static TV* precondition(mg_handle* h) {
     LevelBuf& L0 = h->lv[0];
-    const bool mixed = h->prm.precision != MG_FP64;
-    if (mixed) {
-      const int e = tm_begin(h);
-      k_cast<TV, double><<<lin_blocks(h, L0.g.len), 256, 0, h->s>>>(h->cr, V(L0.b), L0.g.len);
-      ++h->launches;
-      tm_end(h, e, MG_K_CAST, 0, (double)L0.g.npts());
+    h->rz_fused = false;
+    const int zc = vcycle(h, 0, true);
+    if (!h->rz_fused) {
+      const int nb = linear<true>(h, L0.g.len, LinDot<TV>{h->cr, V(L0.x[zc])}, MG_K_DOT);
+      finish(h, nb, FIN_RZ);
     }
-    const int zc = vcycle(h, 0);
     return V(L0.x[zc]);
+  }
+
+  // float32 copy of the float64 residual as the V-cycle's finest right-hand side
+  static void cast_rhs(mg_handle* h) {
+    LevelBuf& L0 = h->lv[0];
+    if (h->prm.precision == MG_FP64) return;
+    const int e = tm_begin(h, MG_K_CAST, 0);
+    launch(h, k_cast<TV, double>, dim3(lin_blocks(h, L0.g.len)), dim3(256), 0, (const double*)h->cr, V(L0.b),
+           L0.g.len);
+    ++h->launches;
+    tm_end(h, e, MG_K_CAST, 0, (double)L0.g.npts());
   }
 };
 
@@ -417,6 +657,8 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
         N[a] = (N[a] - 1) / 2 + 1;
       }
   }
+  if (h->lv[0].g.len >= (i64)1 << 31)
+    return fail(h, MG_ERR_ARG, "grid too large: padded arrays must stay below 2^31 elements");
   const Geom& gc = h->lv[L - 1].g;
   h->nc = (int)gc.npts();
   if (h->nc > MG_MAX_COARSE) return fail(h, MG_ERR_ARG, "coarsest level exceeds MG_MAX_COARSE unknowns");
@@ -424,6 +666,19 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   h->lb = L - 1;
   while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
 
+  {
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    h->bot_smem_budget = optin > 24 * 1024 ? optin - 24 * 1024 : 0;  // room for the static arrays
+    dispatch(h, [&](auto impl) {
+      using I = decltype(impl);
+      cudaFuncSetAttribute(k_bottom<typename I::TVt, typename I::TVt, typename I::TCt>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, h->bot_smem_budget);
+      return 0;
+    });
+    cudaGetLastError();
+  }
   const bool mixed = p.precision != MG_FP64;
   const size_t vb = vbytes(h), cb = cbytes(h);
   // cells
@@ -527,10 +782,35 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
     CKL();
   }
   if (!mixed) h->lv[0].b = h->cr;  // the V-cycle's finest right-hand side is the CG residual
+  // TMA-staged stencil kernels on the levels above the bottom kernel
+  for (int l = 0; l < h->lb; ++l) {
+    const bool want = p.stencil_kernel == 2;
+    if (!want) continue;
+    const bool ok = dispatch(h, [&](auto impl) { return decltype(impl)::tma_prepare(h, l); });
+    if (!ok && p.stencil_kernel == 2) return fail(h, MG_ERR_CUDA, "TMA tensor map encoding failed");
+  }
+  CKL();
   // reduction scratch: enough for every reducing launch on the finest level
   int kcz;
   dim3 gz = zm_grid(h, h->lv[0].g, &kcz);
+  {
+    // one full wave of the pointwise kernels: SMs x resident blocks of the
+    // heaviest one (the CG update)
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_linear<LinCgUpd<float, true, true>, true>, LIN_THREADS, 0);
+    if (per_sm < 1) per_sm = 4;
+    const i64 want = (h->lv[0].g.len / 4 + LIN_THREADS - 1) / LIN_THREADS;
+    const i64 wave = (i64)h->nsm * per_sm;
+    h->lin_grid = (int)(want < wave ? want : wave);
+    if (h->lin_grid < 1) h->lin_grid = 1;
+  }
   h->pstride = gz.x * gz.y * gz.z;
+  if (h->pstride < h->lin_grid) h->pstride = h->lin_grid;
+  if (h->lv[0].tma) {
+    const int tg = h->lv[0].tma_grid[0] * h->lv[0].tma_grid[1] * h->lv[0].tma_grid[2];
+    if (h->pstride < tg) h->pstride = tg;
+  }
   AL(h->partials, double, 2 * (i64)h->pstride);
   AL(h->dsc, Scal, 1);
   // coarsest operator: dense float64 assembly and Cholesky factorisation
@@ -565,7 +845,7 @@ void release(mg_handle* h) {
 // Runs the V-cycle (and, in mixed precision, the casts around it); through a
 // CUDA graph captured on first use when the handle enables graphs.
 template <class I, class TV> mg_status run_precondition(mg_handle* h, TV** z) {
-  if (!h->prm.use_graph) {
+  if (!h->prm.use_graph || h->timing) {  // timed launches run eagerly: plain stream events
     *z = I::precondition(h);
     CKL();
     return MG_OK;
@@ -621,10 +901,15 @@ struct Guard {
 template <class I, bool FLEX, class TV>
 mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
   // p = z + beta p;  q = A p, p.q -> alpha;  x += alpha p, r -= alpha q, r.r (and r.z_old)
-  zmarch<false>(h, g, OpPUpd<TV>{z, h->cp, h->dsc, 0.0}, MG_K_CG_DIR, 0);
+  linear<false>(h, g.len, LinPUpd<TV>{z, h->cp, h->dsc, 0.0}, MG_K_CG_DIR);
   int nb = zmarch<true>(h, g, OpApplyPQ{h->cp, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64}, MG_K_CG_APPLY, 0);
   finish(h, nb, FIN_PQ);
-  nb = zmarch<true>(h, g, OpCgUpd<TV, FLEX>{h->cx, h->cr, h->cp, h->cq, z, h->dsc, 0.0}, MG_K_CG_UPD, 0);
+  if (h->prm.precision == MG_FP64)
+    nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, false>{h->cx, h->cr, h->cp, h->cq, z, nullptr, h->dsc, 0.0},
+                      MG_K_CG_UPD);
+  else
+    nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, true>{h->cx, h->cr, h->cp, h->cq, z, (float*)L0.b, h->dsc, 0.0},
+                      MG_K_CG_UPD);
   finish(h, nb, FIN_RR);
   return MG_OK;
 }
@@ -642,7 +927,7 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
   CK(cudaMemsetAsync(h->cx, 0, (size_t)g.len * 8, h->s));
   CK(cudaMemsetAsync(h->cp, 0, (size_t)g.len * 8, h->s));
   CK(cudaMemsetAsync(h->dsc, 0, sizeof(Scal), h->s));
-  int nb = zmarch<true>(h, g, OpDot<double>{h->cb, h->cb});
+  int nb = linear<true>(h, g.len, LinDot<double>{h->cb, h->cb});
   finish(h, nb, FIN_BB);
   if (p.nonzero_guess) {
     if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
@@ -663,9 +948,8 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
   if (bb > 0) h->hist.push_back(std::sqrt(rr / bb));
   if (bb > 0 && rr > tol2) {
     TV* z = nullptr;
+    I::cast_rhs(h);
     if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
-    nb = zmarch<true>(h, g, OpDot<TV>{h->cr, z}, MG_K_DOT, 0);
-    finish(h, nb, FIN_RZ0);
     for (it = 1; it <= p.maxit; ++it) {
       if (p.flexible) cg_iteration<I, true>(h, z, g, L0);
       else cg_iteration<I, false>(h, z, g, L0);
@@ -673,6 +957,10 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
       sc = *h->hsc;
       if (sc.status & 1) {
         result = fail(h, MG_ERR_NONFINITE, "non-finite value during the iteration");
+        break;
+      }
+      if (sc.status & ST_TIMEOUT) {
+        result = fail(h, MG_ERR_DEVICE_TIMEOUT, "a bounded wait in a TMA-staged kernel gave up");
         break;
       }
       if (sc.status & 2) {
@@ -687,8 +975,6 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
         break;
       }
       if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
-      nb = zmarch<true>(h, g, OpDot<TV>{h->cr, z}, MG_K_DOT, 0);
-      finish(h, nb, FIN_RZ);
     }
     if (it > p.maxit) it = p.maxit;
   }
@@ -730,6 +1016,8 @@ mg_status mg_params_default(mg_params* p) {
   p->flexible = -1;
   p->telescope_max_n = 4096;
   p->use_graph = 1;
+  p->stencil_kernel = 0;
+  p->use_pdl = 1;
   return MG_OK;
 }
 
@@ -745,7 +1033,7 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   if (p.nu_pre < 0 || p.nu_post < 0 || p.cheby_degree < 1 || p.maxit < 0 || !(p.eig_hi > 0) ||
       !(p.eig_lo_frac > 0 && p.eig_lo_frac < 1) || p.coarse_k_rule < 0 || p.coarse_k_rule > 2 || p.face_rule < 0 ||
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
-      p.levels > MG_MAX_LEVELS)
+      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 2)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   if (p.flexible < 0) p.flexible = p.precision == MG_FP64 ? 0 : 1;
   mg_handle* h = new (std::nothrow) mg_handle();
@@ -892,13 +1180,7 @@ mg_status mg_residual_restrict(mg_handle* h, int l, const double* b, const doubl
   if ((s = pack_level(h, l, b, Lv.b, false)) != MG_OK) return s;
   if ((s = pack_level(h, l, x, Lv.x[0], false)) != MG_OK) return s;
   dispatch(h, [&](auto impl) {
-    using I = decltype(impl);
-    using TV = std::remove_pointer_t<decltype(I::V(nullptr))>;
-    using TC = std::remove_const_t<std::remove_pointer_t<decltype(I::C(nullptr))>>;
-    OpResidual<TV, TV, TV, TC> res{I::V(Lv.x[0]), I::V(Lv.b), I::V(Lv.r), I::C(Lv.kx), I::C(Lv.ky), I::C(Lv.kz)};
-    zmarch<false>(h, Lv.g, res);
-    OpRestrict<TV, TV> rs{Lv.g, I::V(Lv.r), I::V(Cv.b)};
-    zmarch<false>(h, Cv.g, rs);
+    decltype(impl)::residual_restrict(h, l, 0);
     return 0;
   });
   CKL();
@@ -944,7 +1226,10 @@ mg_status mg_vcycle(mg_handle* h, const double* r, double* z) {
   Guard guard(h);
   mg_status s;
   if ((s = pack_level(h, 0, r, h->cr, true)) != MG_OK) return s;
-  void* zp = dispatch(h, [&](auto impl) { return (void*)decltype(impl)::precondition(h); });
+  void* zp = dispatch(h, [&](auto impl) {
+    decltype(impl)::cast_rhs(h);
+    return (void*)decltype(impl)::precondition(h);
+  });
   CKL();
   return unpack_level(h, 0, zp, z, false);
 }
@@ -1050,7 +1335,8 @@ mg_status mg_residual_norm_noalloc(mg_handle* h, const double* f, const double* 
   return MG_OK;
 }
 
-mg_status mg_timing_enable(mg_handle* h, int on) {
+mg_status mg_timing_enable(mg_handle* h, int class_mask, int level_mask) {
+  const int on = class_mask != 0;
   if (!h) return MG_ERR_ARG;
   CK(cudaStreamSynchronize(h->s));
   if (on && h->evpool.empty()) {
@@ -1061,7 +1347,9 @@ mg_status mg_timing_enable(mg_handle* h, int on) {
     cudaGraphExecDestroy(h->vexec);
     h->vexec = nullptr;
   }
-  h->timing = on != 0;
+  h->timing = on;
+  h->t_cls_mask = class_mask;
+  h->t_lvl_mask = level_mask;
   h->graph_recs.clear();
   h->pending.clear();
   h->ev_graph_end = h->ev_next = 0;

@@ -58,33 +58,32 @@ template <bool NC, class T> __device__ __forceinline__ T ldp(const T* p) {
   else return *p;
 }
 
+// Programmatic dependent launch: a kernel launched while the previous one in
+// the stream is still finishing waits here before touching global memory
+// (a no-op for ordinary launches), and lets the next kernel launch once its
+// own main loop is done.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------ loaders
 template <bool NC, class R, class T> struct LdVec {
   const T* a;
-  __device__ __forceinline__ R operator()(i64 q) const { return cvt<R>(ldp<NC>(a + q)); }
+  __device__ __forceinline__ R operator()(int q) const { return cvt<R>(ldp<NC>(a + q)); }
 };
 // First Chebyshev iterate from a zero guess: x_1 = D^-1 b / theta.
 template <bool NC, class R, class TV> struct LdJac {
   const TV* b;
   const TV* dinv;
   R inv_theta;
-  __device__ __forceinline__ R operator()(i64 q) const {
+  __device__ __forceinline__ R operator()(int q) const {
     return inv_theta * (cvt<R>(ldp<NC>(dinv + q)) * cvt<R>(ldp<NC>(b + q)));
   }
 };
-// CG search direction formed on the fly: p_new = z + beta p_old.
-template <bool NC> struct LdDir {
-  const double* z;
-  const double* p;
-  double beta;
-  __device__ __forceinline__ double operator()(i64 q) const { return fma(beta, ldp<NC>(p + q), ldp<NC>(z + q)); }
-};
-
 // S_p = sum_q c_pq u_q and D_p = sum_q c_pq at interior point p.
 template <bool NC, class R, class TC, class U>
-__device__ __forceinline__ R stencil(const Geom& g, i64 p, const U& u, const TC* kx, const TC* ky, const TC* kz,
+__device__ __forceinline__ R stencil(const Geom& g, int p, const U& u, const TC* kx, const TC* ky, const TC* kz,
                                      R& D) {
-  const i64 sy = g.Px, sz = g.sz;
+  const int sy = g.Px, sz = (int)g.sz;
   const R cxm = cvt<R>(ldp<NC>(kx + p - 1)), cxp = cvt<R>(ldp<NC>(kx + p));
   const R cym = cvt<R>(ldp<NC>(ky + p - sy)), cyp = cvt<R>(ldp<NC>(ky + p));
   const R czm = cvt<R>(ldp<NC>(kz + p - sz)), czp = cvt<R>(ldp<NC>(kz + p));
@@ -104,11 +103,12 @@ __device__ __forceinline__ R stencil(const Geom& g, i64 p, const U& u, const TC*
 
 // y = A u
 template <class R, class TV, class TC> struct OpApply {
+  using Real = R;
   const TV* u;
   TV* y;
   const TC *kx, *ky, *kz;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, i64 p, double&, double&) const {
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double&, double&) const {
     R D;
     LdVec<NC, R, TV> lu{u};
     R S = stencil<NC, R>(g, p, lu, kx, ky, kz, D);
@@ -121,6 +121,7 @@ template <class R, class TV, class TC> struct OpApply {
 //   s_j = D^-1 (b - A x_j)  evaluated as  D^-1 (b + S) - x_j  (D^-1 D = 1)
 //   d_j = s_j / theta (j = 0)  or  c1 d_{j-1} + c2 s_j,  x_{j+1} = x_j + d_j.
 template <class R, class TV, class TC> struct OpChebStep {
+  using Real = R;
   const TV* x;
   const TV* dprev;  // null for j = 0
   const TV* b;
@@ -130,15 +131,21 @@ template <class R, class TV, class TC> struct OpChebStep {
   const TC *kx, *ky, *kz;
   R c1, c2, inv_theta;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, i64 p, double&, double&) const {
+  // performs the step at p and returns x_{j+1}
+  template <bool NC> __device__ __forceinline__ R step(const Geom& g, int p) const {
     R D;
     LdVec<NC, R, TV> lx{x};
     R S = stencil<NC, R>(g, p, lx, kx, ky, kz, D);
     const R xp = lx(p);
     const R s = fma(cvt<R>(ldp<NC>(dinv + p)), cvt<R>(ldp<NC>(b + p)) + S, -xp);
     const R dn = dprev ? fma(c1, cvt<R>(ldp<NC>(dprev + p)), c2 * s) : s * inv_theta;
-    xout[p] = store_as<TV>(xp + dn);
+    const R xn = xp + dn;
+    xout[p] = store_as<TV>(xn);
     if (dout) dout[p] = store_as<TV>(dn);
+    return xn;
+  }
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double&, double&) const {
+    step<NC>(g, p);
   }
 };
 
@@ -146,6 +153,7 @@ template <class R, class TV, class TC> struct OpChebStep {
 //   x_1 = d_0 = D^-1 b / theta (formed on the fly at the 7 stencil points),
 //   s_1 = D^-1 (b - A x_1), d_1 = c1 d_0 + c2 s_1, x_2 = x_1 + d_1.
 template <class R, class TV, class TC> struct OpChebZero {
+  using Real = R;
   const TV* b;
   const TV* dinv;
   TV* xout;
@@ -153,7 +161,7 @@ template <class R, class TV, class TC> struct OpChebZero {
   const TC *kx, *ky, *kz;
   R c1, c2, inv_theta;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, i64 p, double&, double&) const {
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double&, double&) const {
     R D;
     LdJac<NC, R, TV> lx{b, dinv, inv_theta};
     R S = stencil<NC, R>(g, p, lx, kx, ky, kz, D);
@@ -167,24 +175,26 @@ template <class R, class TV, class TC> struct OpChebZero {
 
 // Degree-1 sweep from a zero guess: x_1 = D^-1 b / theta.
 template <class R, class TV> struct OpChebZero1 {
+  using Real = R;
   const TV* b;
   const TV* dinv;
   TV* xout;
   R inv_theta;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int, int, int, i64 p, double&, double&) const {
+  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int, int, int, int p, double&, double&) const {
     xout[p] = store_as<TV>(inv_theta * (cvt<R>(ldp<NC>(dinv + p)) * cvt<R>(ldp<NC>(b + p))));
   }
 };
 
 // r = b - A x
 template <class R, class TV, class TB, class TC> struct OpResidual {
+  using Real = R;
   const TV* x;
   const TB* b;
   TV* r;
   const TC *kx, *ky, *kz;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, i64 p, double& acc,
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double& acc,
                                                         double&) const {
     R D;
     LdVec<NC, R, TV> lx{x};
@@ -199,20 +209,21 @@ template <class R, class TV, class TB, class TC> struct OpResidual {
 // around fine point (2i+1, 2j+1, 2k+1), the image of coarse point (i,j,k).
 // Runs over the coarse grid; gf is the fine geometry.
 template <class R, class TV> struct OpRestrict {
+  using Real = R;
   Geom gf;
   const TV* r;
   TV* bc;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int i, int j, int k, i64 pc, double&,
+  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int i, int j, int k, int pc, double&,
                                                         double&) const {
-    const i64 pf = gf.at(2 * i + 1, 2 * j + 1, 2 * k + 1);
+    const int pf = (int)gf.at(2 * i + 1, 2 * j + 1, 2 * k + 1);
     R acc = 0;
 #pragma unroll
     for (int c = -1; c <= 1; ++c) {
       R plane = 0;
 #pragma unroll
       for (int b = -1; b <= 1; ++b) {
-        const i64 q = pf + c * gf.sz + b * (i64)gf.Px;
+        const int q = pf + c * (int)gf.sz + b * gf.Px;
         const R row = fma((R)0.5, cvt<R>(ldp<NC>(r + q)),
                           (R)0.25 * (cvt<R>(ldp<NC>(r + q - 1)) + cvt<R>(ldp<NC>(r + q + 1))));
         plane = fma(b == 0 ? (R)0.5 : (R)0.25, row, plane);
@@ -228,14 +239,16 @@ template <class R, class TV> struct OpRestrict {
 // weight 1/2 each: for odd i both are the coincident coarse point (weight 1),
 // for even i they are its two neighbours; index -1 and n_c are zero pads.
 template <class R, class TV> struct OpProlong {
+  using Real = R;
   Geom gc;
   const TV* e;
   TV* x;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int i, int j, int k, i64 p, double&,
+  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int i, int j, int k, int p, double&,
                                                         double&) const {
     const int i0 = (i - 1) >> 1, i1 = i >> 1, j0 = (j - 1) >> 1, j1 = j >> 1, k0 = (k - 1) >> 1, k1 = k >> 1;
-    const i64 a00 = gc.at(i0, j0, k0), a10 = gc.at(i0, j1, k0), a01 = gc.at(i0, j0, k1), a11 = gc.at(i0, j1, k1);
+    const int a00 = (int)gc.at(i0, j0, k0), a10 = (int)gc.at(i0, j1, k0), a01 = (int)gc.at(i0, j0, k1),
+              a11 = (int)gc.at(i0, j1, k1);
     const int di = i1 - i0;
     R s = cvt<R>(ldp<NC>(e + a00)) + cvt<R>(ldp<NC>(e + a00 + di));
     s += cvt<R>(ldp<NC>(e + a10)) + cvt<R>(ldp<NC>(e + a10 + di));
@@ -252,28 +265,16 @@ struct Scal {
   int pad;
 };
 
-// p = z + beta p in place (beta from the scalar block; z in the V-cycle's
-// vector type).  beta = 0 on the first iteration, where p holds zeros.
-template <class TZ> struct OpPUpd {
-  const TZ* z;
-  double* p;
-  const Scal* sc;
-  double beta;
-  __device__ void prepare() { beta = sc->beta; }
-  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int, int, int, i64 i, double&, double&) const {
-    p[i] = fma(beta, p[i], cvt<double>(ldp<NC>(z + i)));
-  }
-};
-
 // q = A p with the stored float64 diagonal: q = D p - sum_q c_pq p_q;
 // acc0 += p.q.  (8 float64 operations per point.)
 struct OpApplyPQ {
+  using Real = float;  // no spills at 40 registers; float64-pipe bound either way
   const double* p;
   double* q;
   const double* dg;
   const double *kx, *ky, *kz;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, i64 i, double& a0,
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int i, double& a0,
                                                         double&) const {
     double D;
     LdVec<NC, double, double> lp{p};
@@ -285,34 +286,105 @@ struct OpApplyPQ {
   }
 };
 
-// x += alpha p, r -= alpha q; acc0 += r.r and, for the flexible (Polak-Ribiere)
-// beta, acc1 += r_new . z_old (z still holds the previous preconditioned residual).
-template <class TZ, bool FLEX> struct OpCgUpd {
+// ---- linear (pointwise) kernels over whole padded arrays ---------------------
+// Pad slots hold zeros in every vector and stay zero under these updates, so
+// the pointwise CG kernels run over [0, len) with 4 consecutive elements per
+// thread and 16-byte vector accesses (len is a multiple of 8).
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, double v[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(float* p, const double v[4]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+}
+
+// p = z + beta p
+template <class TZ> struct LinPUpd {
+  const TZ* z;
+  double* p;
+  const Scal* sc;
+  double beta;
+  __device__ void prepare() { beta = sc->beta; }
+  __device__ __forceinline__ void pt4(i64 t, double&, double&) const {
+    double zv[4], pv[4];
+    ld4(z + t, zv);
+    ld4(p + t, pv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pv[u] = fma(beta, pv[u], zv[u]);
+    st4(p + t, pv);
+  }
+};
+
+// x += alpha p, r -= alpha q, acc0 += r.r, acc1 += r.z_old (FLEX); with B32
+// also b32 = (float) r, the float32 right-hand side of the next V-cycle.
+template <class TZ, bool FLEX, bool B32> struct LinCgUpd {
   double* x;
   double* r;
   const double* p;
   const double* q;
   const TZ* z;
+  float* b32;
   const Scal* sc;
   double alpha;
   __device__ void prepare() { alpha = sc->alpha; }
-  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int, int, int, i64 i, double& a0,
-                                                        double& a1) const {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double rv = fma(-alpha, q[i], r[i]);
-    r[i] = rv;
-    a0 = fma(rv, rv, a0);
-    if constexpr (FLEX) a1 = fma(rv, cvt<double>(ldp<NC>(z + i)), a1);
+  __device__ __forceinline__ void pt4(i64 t, double& a0, double& a1) const {
+    double xv[4], rv[4], pv[4], qv[4];
+    ld4(x + t, xv);
+    ld4(r + t, rv);
+    ld4(p + t, pv);
+    ld4(q + t, qv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xv[u] = fma(alpha, pv[u], xv[u]);
+      rv[u] = fma(-alpha, qv[u], rv[u]);
+      a0 = fma(rv[u], rv[u], a0);
+    }
+    if constexpr (FLEX) {
+      double zv[4];
+      ld4(z + t, zv);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a1 = fma(rv[u], zv[u], a1);
+    }
+    st4(x + t, xv);
+    st4(r + t, rv);
+    if constexpr (B32) st4(b32 + t, rv);
   }
 };
 
-// acc0 += a.b with b in the V-cycle's vector type
-template <class TB> struct OpDot {
+// acc0 += a.b
+template <class TB> struct LinDot {
   const double* a;
   const TB* b;
   __device__ void prepare() {}
-  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int, int, int, i64 i, double& a0, double&) const {
-    a0 = fma(ldp<NC>(a + i), cvt<double>(ldp<NC>(b + i)), a0);
+  __device__ __forceinline__ void pt4(i64 t, double& a0, double&) const {
+    double av[4], bv[4];
+    ld4(a + t, av);
+    ld4(b + t, bv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a0 = fma(av[u], bv[u], a0);
+  }
+};
+
+// Final post-smoothing step on the finest level with the CG dot product
+// rho = r.z fused in: z = x_{j+1} is the V-cycle output, r the float64 residual.
+template <class R, class TV, class TC> struct OpChebStepDot {
+  using Real = R;
+  OpChebStep<R, TV, TC> step;
+  const double* r;
+  __device__ void prepare() {}
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double& a0,
+                                                        double&) const {
+    const R xn = step.template step<NC>(g, p);
+    a0 = fma(ldp<NC>(r + p), (double)store_as<TV>(xn), a0);
   }
 };
 

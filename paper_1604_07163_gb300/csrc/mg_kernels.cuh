@@ -7,13 +7,18 @@ namespace mgdev {
 
 constexpr int ZM_THREADS = 256;  // z-marching tile: 32 (x) by 8 (y) columns
 constexpr int ZM_TX = 32, ZM_TY = 8;
+// Resident blocks per SM requested from the compiler: 4 (64 registers per
+// thread).  Capping registers lower raises occupancy but costs more in
+// per-thread load overlap than it gains (measured on the finest smoother step).
+template <class Op> struct ZmMinBlocks { static constexpr int value = 4; };
 
 // Multi-block z-marching driver: each thread owns one (i, j) column of a
 // 32 x 8 tile and walks planes [k0, k1).  With RED the per-thread sums are
 // reduced per block and written to partials[blockLinear] (and
 // partials[stride + blockLinear] for the second sum).
 template <class Op, bool RED>
-__global__ void __launch_bounds__(ZM_THREADS) k_zmarch(Op op, Geom g, int kchunk, double* partials, int stride) {
+__global__ void __launch_bounds__(ZM_THREADS, ZmMinBlocks<Op>::value) k_zmarch(Op op, Geom g, int kchunk, double* partials, int stride) {
+  pdl_wait();
   op.prepare();
   const int i = blockIdx.x * ZM_TX + (threadIdx.x & 31);
   const int j = blockIdx.y * ZM_TY + (threadIdx.x >> 5);
@@ -21,9 +26,11 @@ __global__ void __launch_bounds__(ZM_THREADS) k_zmarch(Op op, Geom g, int kchunk
   const int k1 = min(k0 + kchunk, g.nz);
   double a0 = 0.0, a1 = 0.0;
   if (i < g.nx && j < g.ny) {
-    i64 p = g.at(i, j, k0);
-    for (int k = k0; k < k1; ++k, p += g.sz) op.template pt<true>(g, i, j, k, p, a0, a1);
+    int p = (int)g.at(i, j, k0);
+    const int sz = (int)g.sz;
+    for (int k = k0; k < k1; ++k, p += sz) op.template pt<true>(g, i, j, k, p, a0, a1);
   }
+  pdl_trigger();
   if constexpr (RED) {
     block_sum2<ZM_THREADS>(a0, a1);
     if (threadIdx.x == 0) {
@@ -34,17 +41,39 @@ __global__ void __launch_bounds__(ZM_THREADS) k_zmarch(Op op, Geom g, int kchunk
   }
 }
 
-// Single-block loop over all interior points of g (used inside the bottom kernel).
+// Linear driver over whole padded arrays: 4 consecutive elements per thread
+// per step, fixed grid, deterministic per-block sums as in k_zmarch.
+constexpr int LIN_THREADS = 256;
+template <class Op, bool RED>
+__global__ void __launch_bounds__(LIN_THREADS) k_linear(Op op, i64 n, double* partials, int stride) {
+  pdl_wait();
+  op.prepare();
+  double a0 = 0.0, a1 = 0.0;
+  const i64 step = (i64)gridDim.x * LIN_THREADS * 4;
+  for (i64 t = ((i64)blockIdx.x * LIN_THREADS + threadIdx.x) * 4; t < n; t += step) op.pt4(t, a0, a1);
+  pdl_trigger();
+  if constexpr (RED) {
+    block_sum2<LIN_THREADS>(a0, a1);
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = a0;
+      partials[stride + blockIdx.x] = a1;
+    }
+  }
+}
+
+// Single-block loop over all interior points of g (used inside the bottom
+// kernel; levels there are small, so 32-bit index arithmetic suffices).
 template <class Op>
 __device__ __forceinline__ void block_for(const Op& op, const Geom& g) {
-  const i64 n = g.npts();
+  const unsigned nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned n = nx * ny * (unsigned)g.nz;
   double a0 = 0, a1 = 0;
-  for (i64 t = threadIdx.x; t < n; t += blockDim.x) {
-    const int i = (int)(t % g.nx);
-    const i64 r = t / g.nx;
-    const int j = (int)(r % g.ny);
-    const int k = (int)(r / g.ny);
-    op.template pt<false>(g, i, j, k, g.at(i, j, k), a0, a1);
+  for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
+    const unsigned r = t / nx;
+    const int i = (int)(t - r * nx);
+    const int k = (int)(r / ny);
+    const int j = (int)(r - (unsigned)k * ny);
+    op.template pt<false>(g, i, j, k, (int)g.at(i, j, k), a0, a1);
   }
 }
 
@@ -81,6 +110,7 @@ __global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, Ge
 // elementwise conversion of whole padded arrays (pads stay zero)
 template <class TD, class TS>
 __global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, i64 n) {
+  pdl_wait();
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
     dst[t] = store_as<TD>(cvt<double>(src[t]));
 }
@@ -241,6 +271,7 @@ enum FinishMode { FIN_BB = 0, FIN_RR = 1, FIN_RZ0 = 2, FIN_PQ = 3, FIN_RZ = 4, F
 // updates the CG scalars.  One block of 256 threads.
 __global__ void __launch_bounds__(256) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
                                                 int flexible) {
+  pdl_wait();
   double a0 = 0.0, a1 = 0.0;
   for (int t = threadIdx.x; t < n; t += 256) {
     a0 += partials[t];
@@ -274,8 +305,10 @@ __global__ void __launch_bounds__(256) k_finish(const double* partials, int n, i
       break;
     case FIN_RZ: {
       // Fletcher-Reeves: beta = rho_new / rho.  Polak-Ribiere (flexible):
-      // beta = (rho_new - r_new.z_old) / rho.
-      s->beta = flexible ? (a0 - s->rz_old) / s->rho : a0 / s->rho;
+      // beta = (rho_new - r_new.z_old) / rho.  rho = 0 marks the first
+      // iteration of a solve (p = z, beta = 0).
+      if (s->rho == 0.0) s->beta = 0.0;
+      else s->beta = flexible ? (a0 - s->rz_old) / s->rho : a0 / s->rho;
       s->rho_new = a0;
       s->rho = a0;
       if (!isfinite(a0)) s->status |= 1;
@@ -359,6 +392,9 @@ template <class TV, class TC> struct BotLevel {
   const TC *kx, *ky, *kz;
 };
 
+// Arrays of a bottom level, in the order of BotArgs::soff.
+enum BotArray { BA_X0 = 0, BA_X1, BA_D, BA_B, BA_R, BA_DINV, BA_KX, BA_KY, BA_KZ, BA_N };
+
 template <class TV, class TC> struct BotArgs {
   BotLevel<TV, TC> lv[BOT_MAX];
   int nlev;            // levels in this kernel; the last one is the coarsest
@@ -366,6 +402,8 @@ template <class TV, class TC> struct BotArgs {
   double theta, delta, sigma;
   const double* Lc;    // Cholesky factor of the coarsest operator (n x n)
   int nc;
+  int soff[BOT_MAX][BA_N];  // byte offset of the array's copy in dynamic shared memory, -1: stays global
+  int result_cur;           // buffer of the first level that holds the result (copied back)
 };
 
 template <class R, class TV, class TC>
@@ -455,8 +493,53 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
 }
 
 // out_cur[0] receives the buffer index holding the result on the first level.
+// Copies n bytes (a multiple of 16) between 16-byte aligned buffers.
+__device__ __forceinline__ void block_copy16(void* dst, const void* src, int n) {
+  for (int t = threadIdx.x; t < n / 16; t += blockDim.x) ((uint4*)dst)[t] = ((const uint4*)src)[t];
+}
+__device__ __forceinline__ void block_zero16(void* dst, int n) {
+  for (int t = threadIdx.x; t < n / 16; t += blockDim.x) ((uint4*)dst)[t] = make_uint4(0, 0, 0, 0);
+}
+
 template <class R, class TV, class TC>
-__global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> a) {
+__global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> ga) {
+  pdl_wait();
+  // Stage the arrays that fit into shared memory: coefficients, D^-1 and the
+  // right-hand side of the first level are copied in, work vectors start as
+  // zeros (their pads must be zero); the kernel then runs on the staged copies.
+  extern __shared__ __align__(16) unsigned char bsm[];
+  __shared__ BotArgs<TV, TC> a;
+  if (threadIdx.x == 0) a = ga;
+  __syncthreads();
+  for (int l = 0; l < ga.nlev; ++l) {
+    const int bytes_v = (int)(ga.lv[l].g.len * (i64)sizeof(TV)), bytes_c = (int)(ga.lv[l].g.len * (i64)sizeof(TC));
+    const BotLevel<TV, TC>& G = ga.lv[l];
+    const void* src[BA_N] = {G.x[0], G.x[1], G.d, G.b, G.r, G.dinv, G.kx, G.ky, G.kz};
+    for (int q = 0; q < BA_N; ++q) {
+      const int off = ga.soff[l][q];
+      if (off < 0) continue;
+      void* dst = bsm + off;
+      const int nb = q >= BA_KX ? bytes_c : bytes_v;
+      const bool copy_in = q >= BA_DINV || (q == BA_B && l == 0);
+      if (copy_in) block_copy16(dst, src[q], nb);
+      else block_zero16(dst, nb);
+      if (threadIdx.x == 0) {
+        BotLevel<TV, TC>& S = a.lv[l];
+        switch (q) {
+          case BA_X0: S.x[0] = (TV*)dst; break;
+          case BA_X1: S.x[1] = (TV*)dst; break;
+          case BA_D: S.d = (TV*)dst; break;
+          case BA_B: S.b = (TV*)dst; break;
+          case BA_R: S.r = (TV*)dst; break;
+          case BA_DINV: S.dinv = (const TV*)dst; break;
+          case BA_KX: S.kx = (const TC*)dst; break;
+          case BA_KY: S.ky = (const TC*)dst; break;
+          case BA_KZ: S.kz = (const TC*)dst; break;
+        }
+      }
+    }
+  }
+  __syncthreads();
   int cur[BOT_MAX];
   const int L = a.nlev;
   for (int l = 0; l < L - 1; ++l) {
@@ -486,6 +569,10 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> a) {
     __syncthreads();
     for (int s = 0; s < a.nu_post; ++s) cur[l] = bot_sweep<R>(V, cur[l], false, a);
   }
+  // result of the first level back to its global buffer
+  const int rc = ga.result_cur;
+  if (a.lv[0].x[rc] != ga.lv[0].x[rc])
+    block_copy16(ga.lv[0].x[rc], a.lv[0].x[rc], (int)(ga.lv[0].g.len * (i64)sizeof(TV)));
 }
 
 }  // namespace mgdev

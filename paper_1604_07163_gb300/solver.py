@@ -31,12 +31,15 @@ class Params:
     flexible: int = -1
     telescope_max_n: int = 4096
     use_graph: int = 1
+    stencil_kernel: int = 0
+    use_pdl: int = 1
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
         L.load().mg_params_default(C.byref(p))
         for name in ("levels", "nu_pre", "nu_post", "cheby_degree", "eig_lo_frac", "eig_hi", "coarse_k_rule",
-                     "face_rule", "maxit", "nonzero_guess", "flexible", "telescope_max_n", "use_graph"):
+                     "face_rule", "maxit", "nonzero_guess", "flexible", "telescope_max_n", "use_graph",
+                     "stencil_kernel", "use_pdl"):
             setattr(p, name, getattr(self, name))
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
@@ -226,9 +229,18 @@ class MGSolver:
         self._check(self._lib.mg_gradient(self._h, _ptr(phi), _ptr(lam), _ptr(out)))
         return out
 
-    def timing(self, on: bool = True):
-        """Enable (and reset) or disable per-kernel device-time accounting."""
-        self._check(self._lib.mg_timing_enable(self._h, 1 if on else 0))
+    def timing(self, on: bool = True, classes=None, levels=None):
+        """Enable (and reset) or disable per-kernel device-time accounting,
+        optionally only for the named kernel classes and the given levels."""
+        cmask = 0
+        if on:
+            names = classes or L.KERNEL_CLASSES
+            for n in names:
+                cmask |= 1 << L.KERNEL_CLASSES.index(n)
+        lmask = 0
+        for l in (levels if levels is not None else range(31)):
+            lmask |= 1 << l
+        self._check(self._lib.mg_timing_enable(self._h, cmask, lmask))
 
     def kernel_times(self):
         """{(class, level): (ms, launches, points)} for classes with launches."""

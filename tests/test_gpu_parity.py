@@ -56,10 +56,13 @@ def make(dims, block, rng, params, seed=101):
     return k, O, S
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_step_parity_fp64(gpu_lib, case):
+def test_step_parity_fp64(gpu_lib, case, kernel):
+    """kernel 1: register/L1 z-marching stencil kernels; kernel 2: TMA-staged
+    tiles on every level above the single-block bottom."""
     dims, block, rng, params = CASES[case]
-    k, O, S = make(dims, block, rng, params)
+    k, O, S = make(dims, block, rng, dict(params, stencil_kernel=kernel))
     for l in range(O.levels):
         d = O.level_dims(l)
         assert S.level_shape(l) == d
@@ -152,14 +155,17 @@ def test_flexible_cg_parity(gpu_lib):
     assert abs(st.iters - ito) <= 1 and rel2(N(x), xo) < 1e-10
 
 
-def test_telescoping_and_graph_do_not_change_the_result(gpu_lib):
-    """Running coarse levels on fewer blocks (down to one block) or replaying
-    the V-cycle from a CUDA graph leaves every point operation unchanged."""
+def test_telescoping_graph_and_kernel_choice_do_not_change_the_result(gpu_lib):
+    """Running coarse levels on fewer blocks (down to one block), replaying
+    the V-cycle from a CUDA graph, or staging tiles with TMA instead of
+    z-marching leaves the result unchanged to rounding."""
     import paper_1604_07163_gb300 as mg
     dims, k, f, spec = mi.workload("poisson33_fp64", 65)
     ref = None
-    for tele, graph in [(0, 0), (4096, 1), (40000, 1), (10 ** 6, 0)]:
-        x, st = mg.MGSolver(T(k), mg.Params(telescope_max_n=tele, use_graph=graph)).solve(T(f), 1e-10)
+    for tele, graph, kern, pdl in [(0, 0, 1, 0), (4096, 1, 0, 1), (40000, 1, 2, 1), (10 ** 6, 0, 0, 1),
+                                   (4096, 1, 2, 0)]:
+        x, st = mg.MGSolver(T(k), mg.Params(telescope_max_n=tele, use_graph=graph, stencil_kernel=kern,
+                                            use_pdl=pdl)).solve(T(f), 1e-10)
         if ref is None:
             ref = (N(x), st.iters)
         else:
@@ -188,12 +194,13 @@ def test_mixed_precision_reaches_fp64_tolerance(gpu_lib, precision):
     assert st.iters <= ito + 6
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("precision,tol", [("mixed_fp32", 2e-6), ("mixed_bf16k", 2e-2)])
-def test_mixed_step_parity(gpu_lib, precision, tol):
+def test_mixed_step_parity(gpu_lib, precision, tol, kernel):
     """float32 vectors: rounding of order 1e-7 relative per step; bfloat16
     coefficients perturb each edge by up to 2^-9 relative."""
     dims = (33, 17, 33)
-    k, O, S = make(dims, 4, 1.0, dict(precision=precision))
+    k, O, S = make(dims, 4, 1.0, dict(precision=precision, stencil_kernel=kernel))
     for l in range(O.levels - 1):
         d = O.level_dims(l)
         x = mi.random_nodal(d, 10 + l)
