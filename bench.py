@@ -118,12 +118,40 @@ def dist_env():
     return rank, world, local
 
 
-def config_dict(spec, n_ranks, iters=None):
+# ---- replicas: every rank solves its own problem; only timing is combined
+def replica_seed(spec, rank: int) -> int:
+    """Seed of rank's independent problem (the workload's seed shifted by the rank)."""
+    return spec["seed"] + rank
+
+
+def max_over_ranks(x: float, device) -> float:
+    """Largest value over all ranks (the timed region of the slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_dofs_per_s(unknowns_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Unknowns solved by all ranks per second of the slowest rank's step."""
+    return world * unknowns_per_rank / (ms_per_step * 1e-3)
+
+
+def config_dict(spec, n_ranks, iters=None, name=None, face_rule=0, adjoint=False):
     N = spec["N"]
+    levels = 1
+    M = N
+    while (M - 1) % 2 == 0 and (M - 1) // 2 + 1 >= 5:
+        M = (M - 1) // 2 + 1
+        levels += 1
     d = {
-        "workload": f"{WORKLOAD}: {N}^3 vertices ({(N - 2) ** 3} unknowns), log10 k ~ U[{spec['lo']:g},{spec['hi']:g}] "
-                    f"on {spec['block']}^3 cell blocks, f ~ U[-1,1], harmonic-mean edge k, 7 levels, "
-                    f"V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual {spec['rtol']:g}",
+        "workload": f"{name or WORKLOAD}: {N}^3 vertices ({(N - 2) ** 3} unknowns), log10 k ~ U[{spec['lo']:g},{spec['hi']:g}] "
+                    f"on {spec['block']}^3 cell blocks, f ~ U[-1,1], {'arithmetic' if face_rule else 'harmonic'}-mean "
+                    f"edge k, {levels} levels, V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual "
+                    f"{spec['rtol']:g}" + ("; step = forward + adjoint solve with the cell gradient" if adjoint else ""),
         "precision": HEADLINE,
         "l2": "no flush: inputs larger than L2 (each float64 vector 134 MB; working set > 2 GB)",
         "parallelism": "replicas" if n_ranks > 1 else "single GPU",
@@ -194,8 +222,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
-    spec = dict(mi.WORKLOADS[WORKLOAD])
-    seed = spec["seed"] + rank
+    spec = dict(mi.WORKLOADS[args.workload])
+    seed = replica_seed(spec, rank)
     dims = (spec["N"],) * 3
     n = (spec["N"] - 2) ** 3
     k = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed), device=dev)
@@ -209,26 +237,35 @@ def run_ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     forms = {}
     solutions = {}
     roofline = clocks = None
     launches = 0
     run_forms = [HEADLINE] + [fm for fm in args.forms.split(",") if fm in FORMS and fm != HEADLINE]
+    def step(S):
+        x, st = S.solve(f, rtol, raise_on_error=False)
+        if args.adjoint:
+            g = x - phi_obs if phi_obs is not None else x
+            lam, grad, _ = S.solve_adjoint(g.contiguous(), rtol, x)
+        return x, st
+
+    phi_obs = None
+    if args.adjoint:  # loss 0.5 |phi - phi_obs|^2 with phi_obs from the k field of seed + 1
+        kobs = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed + 1), device=dev)
+        So = mg.MGSolver(kobs, mg.Params(precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit))
+        phi_obs, _ = So.solve(f, rtol, raise_on_error=False)
+        So.close()
+        del So
+
     for form in run_forms:
-        S = mg.MGSolver(k, mg.Params(precision=form, maxit=3000))
+        S = mg.MGSolver(k, mg.Params(precision=form, maxit=args.maxit, face_rule=args.face_rule))
         headline = form == HEADLINE
         profile_all = None
         for w in range(args.warmup):
             if headline and w == 0:
                 S.timing(True)  # one fully instrumented warm-up solve: per-kernel breakdown
-            x, st = S.solve(f, rtol)
+            x, st = step(S)
             if headline and w == 0:
                 profile_all = S.kernel_times()
                 S.timing(False)
@@ -243,14 +280,14 @@ def run_ours(args):
         iters = []
         launches_form = 0
         for _ in range(args.steps):
-            x, st = S.solve(f, rtol)
+            x, st = step(S)
             iters.append(st.iters)
             launches_form += st.kernel_launches
         e1.record()
         barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
-        forms[form] = {"value": world * n / (ms * 1e-3), "ms_per_step": ms, "iters": iters[-1],
-                       "true_rel_resid": st.true_rel_resid}
+        ms = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+        forms[form] = {"value": whole_job_dofs_per_s(n, world, ms), "ms_per_step": ms, "iters": iters[-1],
+                       "true_rel_resid": st.true_rel_resid, "status": st.status}
         solutions[form] = x.detach().clone()
         if headline:
             # the same K steps again with CUDA events around every launch of the
@@ -258,7 +295,7 @@ def run_ours(args):
             # slow the whole solve, so the headline steps above run without them)
             S.timing(True, classes=[dom], levels=[0])
             for _ in range(args.steps):
-                S.solve(f, rtol)
+                S.solve(f, rtol, raise_on_error=False)
             torch.cuda.synchronize()
             clocks = sampler.stop()
             launches = launches_form
@@ -274,12 +311,14 @@ def run_ours(args):
             e0.record()
             for _ in range(args.steps):
                 fd.copy_(f_host, non_blocking=True)
-                xe, _ = S.solve(fd, rtol)
+                xe, _ = S.solve(fd, rtol, raise_on_error=False)
+                if args.adjoint:
+                    S.solve_adjoint((xe - phi_obs).contiguous(), rtol, xe)
                 x_host.copy_(xe, non_blocking=True)
             e1.record()
             barrier()
-            ms_e2e = max_over_ranks(e0.elapsed_time(e1)) / args.steps
-            e2e = {"value": world * n / (ms_e2e * 1e-3), "unit": "DOF/s",
+            ms_e2e = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+            e2e = {"value": whole_job_dofs_per_s(n, world, ms_e2e), "unit": "DOF/s",
                    "h2d_bytes_per_step": f_host.numel() * 8, "d2h_bytes_per_step": x_host.numel() * 8}
         S.close()
         del S
@@ -292,7 +331,7 @@ def run_ours(args):
         speedup = forms["fp64"]["ms_per_step"] / forms[HEADLINE]["ms_per_step"]
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.adjoint:
         its = forms.get("fp64", forms[HEADLINE])["iters"]
         sample = 20
         v, dt, cores = oracle_sample(spec, its, sample)
@@ -305,7 +344,8 @@ def run_ours(args):
         "metric": METRIC, "value": forms[HEADLINE]["value"], "unit": "DOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms[HEADLINE]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic", "config": config_dict(spec, world, forms[HEADLINE]["iters"]),
+        "data": "synthetic", "config": config_dict(spec, world, forms[HEADLINE]["iters"], args.workload,
+                                                   args.face_rule, args.adjoint),
         "forms": forms, "speedup_mixed_vs_fp64": speedup,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
@@ -364,8 +404,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default=",".join(FORMS),
                     help="comma-separated subset of " + ",".join(FORMS) + " (the headline form is always run)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(mi.WORKLOADS),
+                    help="synthetic workload (the headline metric is quoted on " + WORKLOAD + ")")
+    ap.add_argument("--face-rule", type=int, default=0, help="edge k: 0 harmonic (default), 1 arithmetic mean")
+    ap.add_argument("--maxit", type=int, default=3000)
+    ap.add_argument("--adjoint", action="store_true", help="each step is a forward + adjoint solve with gradient")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and args.workload == WORKLOAD:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

@@ -1,0 +1,102 @@
+"""Parity at the full workload sizes, in the configuration bench.py times.
+
+At 257^3 (the benchmark workload) and 513^3 the oracle still builds its CSR
+hierarchy in seconds, so the operator is compared on every point; a full
+solve is checked through properties the oracle evaluates itself (its true
+residual of the GPU solution) and a few fixed CG iterations are compared
+iterate by iterate.  The float64 iteration count to tolerance is the one the
+oracle recorded in tests/golden/oracle_solves.json.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import mg_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_solves.json")
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def relmax(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def rel2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def w257():
+    dims, k, f, spec = mi.workload("poisson257_c1e4")
+    return dims, k, f, spec, oracle.Oracle(k)
+
+
+def test_257_operator_every_point(gpu_lib, w257):
+    mg = gpu_lib
+    dims, k, f, spec, O = w257
+    x = mi.random_nodal(dims, 5)
+    Ox = O.apply(x)
+    S64 = mg.MGSolver(T(k))
+    assert relmax(S64.apply(T(x), -1).cpu().numpy(), Ox) < 1e-13
+    assert relmax(S64.apply(T(x), 0).cpu().numpy(), Ox) < 1e-13
+    S32 = mg.MGSolver(T(k), mg.Params(precision="mixed_fp32"))
+    assert relmax(S32.apply(T(x), -1).cpu().numpy(), Ox) < 1e-13  # outer operator stays float64
+    assert relmax(S32.apply(T(x), 0).cpu().numpy(), Ox) < 2e-6
+
+
+def test_257_bench_solve_true_residual_by_oracle(gpu_lib, w257):
+    """The benchmark's headline form (float32 V-cycle in float64 CG) reaches
+    the tolerance on the oracle's own operator."""
+    mg = gpu_lib
+    dims, k, f, spec, O = w257
+    S = mg.MGSolver(T(k), mg.Params(precision="mixed_fp32", maxit=3000))
+    x, st = S.solve(T(f), spec["rtol"])
+    xn = x.cpu().numpy()
+    true = np.linalg.norm((f - O.apply(xn))[1:-1, 1:-1, 1:-1]) / np.linalg.norm(f)
+    assert true <= spec["rtol"] * 1.01
+    assert abs(true - st.true_rel_resid) <= 1e-3 * true
+    # float64 form: iteration count equals the oracle's recorded one (within 1)
+    golden = json.load(open(GOLDEN))["poisson257_c1e4"]
+    x64, st64 = mg.MGSolver(T(k), mg.Params(maxit=3000)).solve(T(f), spec["rtol"])
+    assert abs(st64.iters - golden["iterations"]) <= 1
+    assert rel2(x64.cpu().numpy(), xn) < 1e-6  # both forms agree to the accuracy the tolerance implies
+
+
+def test_257_fixed_iterations_match_oracle(gpu_lib, w257):
+    mg = gpu_lib
+    dims, k, f, spec, O = w257
+    its = 4
+    xo, ito, _ = O.pcg(f, 0.0, maxit=its)
+    x, st = mg.MGSolver(T(k), mg.Params(maxit=its)).solve(T(f), 0.0, raise_on_error=False)
+    assert st.iters == its == ito
+    assert rel2(x.cpu().numpy(), xo) < 1e-12
+
+
+def test_513_operator_fixed_iterations_and_arithmetic_rule_solve(gpu_lib):
+    """513^3, log10 k ~ U[-3,3]: operator on every point and 2 CG iterations
+    under the default (harmonic) rule; with the arithmetic face rule the
+    solve converges and the oracle confirms the residual."""
+    mg = gpu_lib
+    dims, k, f, spec = mi.workload("poisson513_c1e6")
+    O = oracle.Oracle(k)
+    x = mi.random_nodal(dims, 6)
+    S = mg.MGSolver(T(k), mg.Params(maxit=2))
+    assert relmax(S.apply(T(x), -1).cpu().numpy(), O.apply(x)) < 1e-13
+    xo, _, _ = O.pcg(f, 0.0, maxit=2)
+    xg, st = S.solve(T(f), 0.0, raise_on_error=False)
+    assert rel2(xg.cpu().numpy(), xo) < 1e-12
+    del S, O
+    Oa = oracle.Oracle(k, face_rule=1)
+    Sa = mg.MGSolver(T(k), mg.Params(precision="mixed_fp32", face_rule=1, maxit=500))
+    xa, sta = Sa.solve(T(f), spec["rtol"])
+    true = np.linalg.norm((f - Oa.apply(xa.cpu().numpy()))[1:-1, 1:-1, 1:-1]) / np.linalg.norm(f)
+    assert true <= spec["rtol"] * 1.01
