@@ -79,9 +79,13 @@ typedef struct {
   int flexible;        /* CG beta: 0 Fletcher-Reeves, 1 Polak-Ribiere (flexible); -1 = 0 for FP64, 1 for mixed */
   int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
   int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
-  int stencil_kernel;  /* smoother/residual kernels: 0 automatic (currently the z-marching kernels, the
-                          faster of the two on GB300 as measured), 1 register/L1 z-marching everywhere,
-                          2 TMA-staged tiles wherever a level is not in the single-block bottom */
+  int stencil_kernel;  /* smoother/residual kernels on the levels above the single-block bottom:
+                          0 (default) z-marching with neighbours read through L1, and on levels with
+                            at least 64 points per axis the coarse-grid correction folded into the
+                            first post-smoothing step (shared-plane z-marching kernel),
+                          1 z-marching through L1 only,
+                          2 TMA-staged tiles (cp.async.bulk.tensor),
+                          3 shared-plane z-marching for every pass */
   int use_pdl;         /* 1: launch solve kernels as programmatic dependent launches (default 1) */
 } mg_params;
 

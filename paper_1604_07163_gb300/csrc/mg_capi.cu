@@ -16,6 +16,7 @@
 #include "mg.h"
 #include "mg_kernels.cuh"
 #include "mg_tma.cuh"
+#include "mg_zs.cuh"
 
 using namespace mgdev;
 
@@ -32,6 +33,9 @@ struct LevelBuf {
   void* x[2] = {nullptr, nullptr};
   void *d = nullptr, *b = nullptr, *r = nullptr;
   // TMA tensor maps (2-D row views) for the staged stencil kernels
+  bool zs = false;         // 2.5-D shared-plane z-marching kernels for every stencil pass
+  bool zs_prolong = false; // 2.5-D kernel only for the correction folded into the first post-smoothing step
+  int zs_grid[3] = {0, 0, 0}, zs_kchunk = 0;
   bool tma = false;
   CUtensorMap m_full_x[2], m_full_b, m_full_dinv, m_kx, m_ky, m_kz, m_c_dinv, m_c_b, m_c_d, m_c_r64;
   int tma_grid[3] = {0, 0, 0}, tma_kchunk = 0;
@@ -122,6 +126,27 @@ mg_status fail(mg_handle* h, mg_status code, const std::string& msg) {
 #define CKL() CK(cudaGetLastError())
 
 int roundup(int a, int m) { return (a + m - 1) / m * m; }
+
+// Plane split for tiles x zs blocks: the split with the best wave efficiency
+// (blocks / (waves x resident slots)) among those leaving at least min_chunk
+// planes per block; the smaller split wins ties.
+int best_zsplit(int tiles, int slots, int nz, int min_chunk) {
+  int best = 1;
+  double best_eff = -1.0;
+  const int maxz = nz / min_chunk > 1 ? nz / min_chunk : 1;
+  for (int zs = 1; zs <= maxz; ++zs) {
+    const int kc = (nz + zs - 1) / zs;
+    const int z = (nz + kc - 1) / kc;
+    const long long blocks = (long long)tiles * z;
+    const long long waves = (blocks + slots - 1) / slots;
+    const double eff = (double)blocks / (double)(waves * slots);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = z;
+    }
+  }
+  return best;
+}
 
 Geom make_geom(int nx, int ny, int nz) {
   Geom g;
@@ -396,39 +421,42 @@ template <class TV, class TC> struct Impl {
     return grid.x * grid.y * grid.z;
   }
 
-  // One smoother sweep on level l starting from buffer cur; returns the new cur.
-  // With fuse_rz the last step also accumulates rho = r.z for the outer CG
-  // (finest level only) and finishes the CG scalars.
-  static int sweep(mg_handle* h, int l, int cur, bool zero, bool fuse_rz = false) {
+  // ---- 2.5-D shared-plane z-marching launches ---------------------------------
+  static void zs_prepare(mg_handle* h, int l) {
+    LevelBuf& Lv = h->lv[l];
+    const Geom& g = Lv.g;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zs<PolProlongStep0<TV, TV, TC>>, ZS_THREADS, 0);
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const int gx = (g.nx + ZS_TX - 1) / ZS_TX, gy = (g.ny + ZS_TY - 1) / ZS_TY;
+    const int zs = best_zsplit(gx * gy, h->nsm * per_sm, g.nz, 16);
+    Lv.zs_kchunk = (g.nz + zs - 1) / zs;
+    Lv.zs_grid[0] = gx;
+    Lv.zs_grid[1] = gy;
+    Lv.zs_grid[2] = (g.nz + Lv.zs_kchunk - 1) / Lv.zs_kchunk;
+  }
+
+  template <class Pol> static int zs_launch(mg_handle* h, int l, const Pol& pol, int cls) {
+    LevelBuf& Lv = h->lv[l];
+    dim3 grid(Lv.zs_grid[0], Lv.zs_grid[1], Lv.zs_grid[2]);
+    const int e = tm_begin(h, cls, l);
+    launch(h, k_zs<Pol>, grid, dim3(ZS_THREADS), 0, pol, Lv.g, Lv.zs_kchunk, h->partials);
+    ++h->launches;
+    tm_end(h, e, cls, l, (double)Lv.g.npts());
+    return grid.x * grid.y * grid.z;
+  }
+
+  // Chebyshev steps j_from..degree-1 of one sweep on level l: the iterate is in
+  // buffer cur (and d_{j_from-1} in Lv.d when j_from > 0), rho_prev = rho_{j_from-1}.
+  // With fuse_rz the last step also accumulates rho = r.z for the outer CG and
+  // finishes the CG scalars.  Returns the buffer holding the result.
+  static int cheb_steps(mg_handle* h, int l, int cur, int j_from, double rho_prev, bool fuse_rz) {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
     double theta, delta, sigma;
     cheb_consts(p, &theta, &delta, &sigma);
     const TV inv_theta = (TV)(1.0 / theta);
-    double rho_prev = 1.0 / sigma;
-    int j0 = 0;
-    if (zero) {
-      if (p.cheby_degree == 1) {
-        OpChebZero1<TV, TV> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), inv_theta};
-        zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
-        return cur ^ 1;
-      }
-      const double rho = 1.0 / (2.0 * sigma - rho_prev);
-      if (Lv.tma) {
-        tma_launch<TK_ZERO, false, false>(h, l, Lv.m_full_b, &Lv.m_full_dinv, V(Lv.x[cur ^ 1]),
-                                          p.cheby_degree > 2 ? V(Lv.d) : nullptr, rho * rho_prev, 2.0 * rho / delta,
-                                          1.0 / theta, MG_K_CHEB_ZERO);
-      } else {
-        OpChebZero<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), p.cheby_degree > 2 ? V(Lv.d) : nullptr,
-                                  C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(rho * rho_prev), (TV)(2.0 * rho / delta),
-                                  inv_theta};
-        zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
-      }
-      cur ^= 1;
-      rho_prev = rho;
-      j0 = 2;
-    }
-    for (int j = j0; j < p.cheby_degree; ++j) {
+    for (int j = j_from; j < p.cheby_degree; ++j) {
       double c1 = 0.0, c2 = 0.0;
       if (j > 0) {
         const double rho = 1.0 / (2.0 * sigma - rho_prev);
@@ -436,32 +464,96 @@ template <class TV, class TC> struct Impl {
         c2 = 2.0 * rho / delta;
         rho_prev = rho;
       }
-      OpChebStep<TV, TV, TC> op{V(Lv.x[cur]), j > 0 ? V(Lv.d) : nullptr, V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]),
-                                j + 1 < p.cheby_degree ? V(Lv.d) : nullptr, C(Lv.kx), C(Lv.ky), C(Lv.kz),
-                                (TV)c1, (TV)c2, inv_theta};
       const bool dot = fuse_rz && j + 1 == p.cheby_degree;
       TV* xo = V(Lv.x[cur ^ 1]);
       TV* dout = j + 1 < p.cheby_degree ? V(Lv.d) : nullptr;
-      if (Lv.tma) {
+      const TV* dprev = j > 0 ? V(Lv.d) : nullptr;
+      int nb = -1;
+      if (Lv.zs) {
+        if (dot)
+          nb = zs_launch(h, l, PolStep<TV, TV, TC, true>{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx),
+                                                         C(Lv.ky), C(Lv.kz), h->cr, (TV)c1, (TV)c2, inv_theta},
+                         MG_K_CHEB_STEP);
+        else
+          zs_launch(h, l, PolStep<TV, TV, TC, false>{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx),
+                                                      C(Lv.ky), C(Lv.kz), nullptr, (TV)c1, (TV)c2, inv_theta},
+                    MG_K_CHEB_STEP);
+      } else if (Lv.tma) {
         const CUtensorMap& f0 = Lv.m_full_x[cur];
-        int nb;
         if (j > 0 && dot) nb = tma_launch<TK_STEP, true, true>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
-        else if (j > 0) nb = tma_launch<TK_STEP, true, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+        else if (j > 0) tma_launch<TK_STEP, true, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
         else if (dot) nb = tma_launch<TK_STEP, false, true>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
-        else nb = tma_launch<TK_STEP, false, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
-        if (dot) {
-          finish(h, nb, FIN_RZ);
-          h->rz_fused = true;
-        }
-      } else if (dot) {
-        const int nb = zmarch<true>(h, Lv.g, OpChebStepDot<TV, TV, TC>{op, h->cr}, MG_K_CHEB_STEP, l);
+        else tma_launch<TK_STEP, false, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+      } else {
+        OpChebStep<TV, TV, TC> op{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
+                                  (TV)c1, (TV)c2, inv_theta};
+        if (dot) nb = zmarch<true>(h, Lv.g, OpChebStepDot<TV, TV, TC>{op, h->cr}, MG_K_CHEB_STEP, l);
+        else zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
+      }
+      if (dot) {
         finish(h, nb, FIN_RZ);
         h->rz_fused = true;
-      } else {
-        zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
       }
       cur ^= 1;
     }
+    return cur;
+  }
+
+  // One smoother sweep on level l starting from buffer cur; returns the new cur.
+  // With fuse_rz the last step also accumulates rho = r.z for the outer CG.
+  static int sweep(mg_handle* h, int l, int cur, bool zero, bool fuse_rz = false) {
+    LevelBuf& Lv = h->lv[l];
+    const mg_params& p = h->prm;
+    double theta, delta, sigma;
+    cheb_consts(p, &theta, &delta, &sigma);
+    const TV inv_theta = (TV)(1.0 / theta);
+    if (!zero) return cheb_steps(h, l, cur, 0, 1.0 / sigma, fuse_rz);
+    if (p.cheby_degree == 1) {
+      OpChebZero1<TV, TV> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), inv_theta};
+      zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+      return cur ^ 1;
+    }
+    const double rho_prev = 1.0 / sigma;
+    const double rho = 1.0 / (2.0 * sigma - rho_prev);
+    const double c1 = rho * rho_prev, c2 = 2.0 * rho / delta;
+    TV* dout = p.cheby_degree > 2 ? V(Lv.d) : nullptr;
+    if (Lv.zs) {
+      zs_launch(h, l, PolZero<TV, TV, TC>{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
+                                          (TV)c1, (TV)c2, inv_theta},
+                MG_K_CHEB_ZERO);
+    } else if (Lv.tma) {
+      tma_launch<TK_ZERO, false, false>(h, l, Lv.m_full_b, &Lv.m_full_dinv, V(Lv.x[cur ^ 1]), dout, c1, c2,
+                                        1.0 / theta, MG_K_CHEB_ZERO);
+    } else {
+      OpChebZero<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
+                                (TV)c1, (TV)c2, inv_theta};
+      zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+    }
+    return cheb_steps(h, l, cur ^ 1, 2, rho, fuse_rz);
+  }
+
+  // Coarse-grid correction x += P e followed by the post-smoothing sweeps of
+  // level l.  On the 2.5-D kernels the correction is folded into the first
+  // smoother step (u = x + P e is formed per point, x + P e is never stored).
+  static int correct_and_post_smooth(mg_handle* h, int l, int cur, int ccur, bool fuse_rz) {
+    LevelBuf& Lv = h->lv[l];
+    LevelBuf& Cv = h->lv[l + 1];
+    const mg_params& p = h->prm;
+    const bool single_step_dot = fuse_rz && p.nu_post == 1 && p.cheby_degree == 1;
+    if ((Lv.zs || Lv.zs_prolong) && p.nu_post >= 1 && !single_step_dot) {
+      double theta, delta, sigma;
+      cheb_consts(p, &theta, &delta, &sigma);
+      zs_launch(h, l, PolProlongStep0<TV, TV, TC>{Cv.g, V(Lv.x[cur]), V(Cv.x[ccur]), V(Lv.b), V(Lv.dinv),
+                                                  V(Lv.x[cur ^ 1]), p.cheby_degree > 1 ? V(Lv.d) : nullptr,
+                                                  C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(1.0 / theta)},
+                MG_K_PROLONG);
+      cur = cheb_steps(h, l, cur ^ 1, 1, 1.0 / sigma, fuse_rz && p.nu_post == 1);
+      for (int s = 1; s < p.nu_post; ++s) cur = sweep(h, l, cur, false, fuse_rz && s + 1 == p.nu_post);
+      return cur;
+    }
+    OpProlong<TV, TV> pr{Cv.g, V(Cv.x[ccur]), V(Lv.x[cur])};
+    zmarch<false>(h, Lv.g, pr, MG_K_PROLONG, l);
+    for (int s = 0; s < p.nu_post; ++s) cur = sweep(h, l, cur, false, fuse_rz && s + 1 == p.nu_post);
     return cur;
   }
 
@@ -519,7 +611,9 @@ template <class TV, class TC> struct Impl {
   static void residual_restrict(mg_handle* h, int l, int cur) {
     LevelBuf& Lv = h->lv[l];
     LevelBuf& Cv = h->lv[l + 1];
-    if (Lv.tma) {
+    if (Lv.zs) {
+      zs_launch(h, l, PolResid<TV, TV, TC>{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)}, MG_K_RESID);
+    } else if (Lv.tma) {
       tma_launch<TK_RESID, false, false>(h, l, Lv.m_full_x[cur], nullptr, V(Lv.r), nullptr, 0.0, 0.0, 0.0,
                                          MG_K_RESID);
     } else {
@@ -538,16 +632,12 @@ template <class TV, class TC> struct Impl {
       return l == h->L - 1 ? 0 : level_result_cur(h->prm);
     }
     LevelBuf& Lv = h->lv[l];
-    LevelBuf& Cv = h->lv[l + 1];
     int cur = 0;
     for (int s = 0; s < h->prm.nu_pre; ++s) cur = sweep(h, l, cur, s == 0);
     if (h->prm.nu_pre == 0) cudaMemsetAsync(Lv.x[0], 0, (size_t)Lv.g.len * sizeof(TV), h->s);
     residual_restrict(h, l, cur);
     const int ccur = vcycle(h, l + 1);
-    OpProlong<TV, TV> pr{Cv.g, V(Cv.x[ccur]), V(Lv.x[cur])};
-    zmarch<false>(h, Lv.g, pr, MG_K_PROLONG, l);
-    for (int s = 0; s < h->prm.nu_post; ++s) cur = sweep(h, l, cur, false, fuse_rz && s + 1 == h->prm.nu_post);
-    return cur;
+    return correct_and_post_smooth(h, l, cur, ccur, fuse_rz);
   }
 
   // z = M^-1 r; the finest right-hand side (the float64 residual, or its
@@ -784,10 +874,17 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   if (!mixed) h->lv[0].b = h->cr;  // the V-cycle's finest right-hand side is the CG residual
   // TMA-staged stencil kernels on the levels above the bottom kernel
   for (int l = 0; l < h->lb; ++l) {
-    const bool want = p.stencil_kernel == 2;
-    if (!want) continue;
-    const bool ok = dispatch(h, [&](auto impl) { return decltype(impl)::tma_prepare(h, l); });
-    if (!ok && p.stencil_kernel == 2) return fail(h, MG_ERR_CUDA, "TMA tensor map encoding failed");
+    if (p.stencil_kernel == 0 || p.stencil_kernel == 3) {
+      dispatch(h, [&](auto impl) {
+        decltype(impl)::zs_prepare(h, l);
+        return 0;
+      });
+      if (p.stencil_kernel == 3) h->lv[l].zs = true;
+      else h->lv[l].zs_prolong = h->lv[l].g.nx >= 64 && h->lv[l].g.ny >= 64;
+    } else if (p.stencil_kernel == 2) {
+      const bool ok = dispatch(h, [&](auto impl) { return decltype(impl)::tma_prepare(h, l); });
+      if (!ok) return fail(h, MG_ERR_CUDA, "TMA tensor map encoding failed");
+    }
   }
   CKL();
   // reduction scratch: enough for every reducing launch on the finest level
@@ -810,6 +907,10 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   if (h->lv[0].tma) {
     const int tg = h->lv[0].tma_grid[0] * h->lv[0].tma_grid[1] * h->lv[0].tma_grid[2];
     if (h->pstride < tg) h->pstride = tg;
+  }
+  if (h->lv[0].zs || h->lv[0].zs_prolong) {
+    const int zg = h->lv[0].zs_grid[0] * h->lv[0].zs_grid[1] * h->lv[0].zs_grid[2];
+    if (h->pstride < zg) h->pstride = zg;
   }
   AL(h->partials, double, 2 * (i64)h->pstride);
   AL(h->dsc, Scal, 1);
@@ -1033,7 +1134,7 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   if (p.nu_pre < 0 || p.nu_post < 0 || p.cheby_degree < 1 || p.maxit < 0 || !(p.eig_hi > 0) ||
       !(p.eig_lo_frac > 0 && p.eig_lo_frac < 1) || p.coarse_k_rule < 0 || p.coarse_k_rule > 2 || p.face_rule < 0 ||
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
-      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 2)
+      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 3)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   if (p.flexible < 0) p.flexible = p.precision == MG_FP64 ? 0 : 1;
   mg_handle* h = new (std::nothrow) mg_handle();

@@ -62,18 +62,17 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(Op op, i64 n, double* pa
 }
 
 // Single-block loop over all interior points of g (used inside the bottom
-// kernel; levels there are small, so 32-bit index arithmetic suffices).
+// kernel).  The iteration space is padded to powers of two in x and y so the
+// point indices come from shifts and masks instead of divisions.
 template <class Op>
 __device__ __forceinline__ void block_for(const Op& op, const Geom& g) {
-  const unsigned nx = (unsigned)g.nx, ny = (unsigned)g.ny;
-  const unsigned n = nx * ny * (unsigned)g.nz;
+  const int lx = 32 - __clz(g.nx - 1), ly = 32 - __clz(g.ny - 1);  // ceil(log2)
+  const unsigned n = (unsigned)g.nz << (lx + ly);
+  const unsigned mx = (1u << lx) - 1, my = (1u << ly) - 1;
   double a0 = 0, a1 = 0;
   for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
-    const unsigned r = t / nx;
-    const int i = (int)(t - r * nx);
-    const int k = (int)(r / ny);
-    const int j = (int)(r - (unsigned)k * ny);
-    op.template pt<false>(g, i, j, k, (int)g.at(i, j, k), a0, a1);
+    const int i = (int)(t & mx), j = (int)((t >> lx) & my), k = (int)(t >> (lx + ly));
+    if (i < g.nx && j < g.ny) op.template pt<false>(g, i, j, k, (int)g.at(i, j, k), a0, a1);
   }
 }
 
@@ -444,33 +443,41 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
   return cur;
 }
 
-// Coarsest solve x = L^-T L^-1 b in float64.  n <= 32: one warp with shuffles;
-// otherwise the whole block with shared-memory substitution.
+// Coarsest solve x = L^-T L^-1 b in float64 by forward and back substitution
+// with the Cholesky factor.  For n <= 32 the factor is staged in shared
+// memory with its reciprocal pivots and one warp substitutes with shuffles
+// (one multiply-add per step); larger n use the whole block.
 template <class TV>
 __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, int n) {
   __shared__ double y[1024];
+  __shared__ double Ls[32 * 33];
+  __shared__ double rpiv[32];
   for (int u = threadIdx.x; u < n; u += blockDim.x) {
     const int i = u % g.nx, j = (u / g.nx) % g.ny, k = u / (g.nx * g.ny);
     y[u] = cvt<double>(b[g.at(i, j, k)]);
   }
-  __syncthreads();
   if (n <= 32) {
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ls[(t / n) * 33 + t % n] = Lc[t];
+    __syncthreads();
     if (threadIdx.x < 32) {
       const int l = threadIdx.x;
+      if (l < n) rpiv[l] = 1.0 / Ls[l * 33 + l];
+      __syncwarp();
       double v = l < n ? y[l] : 0.0;
       for (int c = 0; c < n; ++c) {  // forward: L y = b
-        const double yc = __shfl_sync(0xffffffffu, v, c) / Lc[(i64)c * n + c];
+        const double yc = __shfl_sync(0xffffffffu, v, c) * rpiv[c];
         if (l == c) v = yc;
-        if (l > c && l < n) v -= Lc[(i64)l * n + c] * yc;
+        if (l > c && l < n) v = fma(-Ls[l * 33 + c], yc, v);
       }
       for (int c = n - 1; c >= 0; --c) {  // backward: L^T x = y
-        const double xc = __shfl_sync(0xffffffffu, v, c) / Lc[(i64)c * n + c];
+        const double xc = __shfl_sync(0xffffffffu, v, c) * rpiv[c];
         if (l == c) v = xc;
-        if (l < c) v -= Lc[(i64)c * n + l] * xc;
+        if (l < c) v = fma(-Ls[c * 33 + l], xc, v);
       }
       if (l < n) y[l] = v;
     }
   } else {
+    __syncthreads();
     for (int c = 0; c < n; ++c) {
       if (threadIdx.x == 0) y[c] /= Lc[(i64)c * n + c];
       __syncthreads();
@@ -495,7 +502,9 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
 // out_cur[0] receives the buffer index holding the result on the first level.
 // Copies n bytes (a multiple of 16) between 16-byte aligned buffers.
 __device__ __forceinline__ void block_copy16(void* dst, const void* src, int n) {
-  for (int t = threadIdx.x; t < n / 16; t += blockDim.x) ((uint4*)dst)[t] = ((const uint4*)src)[t];
+  const int m = n / 16;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < m; t += blockDim.x) ((uint4*)dst)[t] = ((const uint4*)src)[t];
 }
 __device__ __forceinline__ void block_zero16(void* dst, int n) {
   for (int t = threadIdx.x; t < n / 16; t += blockDim.x) ((uint4*)dst)[t] = make_uint4(0, 0, 0, 0);

@@ -56,11 +56,12 @@ def make(dims, block, rng, params, seed=101):
     return k, O, S
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_step_parity_fp64(gpu_lib, case, kernel):
-    """kernel 1: register/L1 z-marching stencil kernels; kernel 2: TMA-staged
-    tiles on every level above the single-block bottom."""
+    """kernel 0: default (L1 z-marching, prolongation folded into the first
+    post-smoothing step on large levels); 1: L1 z-marching only; 2: TMA-staged
+    tiles; 3: shared-plane z-marching for every pass."""
     dims, block, rng, params = CASES[case]
     k, O, S = make(dims, block, rng, dict(params, stencil_kernel=kernel))
     for l in range(O.levels):
@@ -105,21 +106,23 @@ def test_gradient_kernel_parity(gpu_lib):
         assert relmax(N(S.gradient(T(phi), T(lam))), O.gradient(phi, lam)) < 1e-13
 
 
-@pytest.mark.parametrize("name,n,tol", [("poisson33_fp64", None, 1e-10), ("adjoint129", None, 1e-10),
-                                        ("poisson257_c1e4", 65, 2e-9)])
-def test_solve_parity_fp64(gpu_lib, name, n, tol):
+@pytest.mark.parametrize("name,n,tol,dit", [("poisson33_fp64", None, 1e-10, 1), ("adjoint129", None, 1e-10, 1),
+                                            ("poisson257_c1e4", 65, 2e-9, 2)])
+def test_solve_parity_fp64(gpu_lib, name, n, tol, dit):
     """The two FP64 runs differ only in rounding order (tree vs sequential dot
     products, fused multiply-adds).  CG amplifies that difference with the
     condition number: at 10^2 contrast (33^3, 129^3) the solutions agree to
-    1e-10; at 10^4 contrast the amplification reaches a few 1e-10 after ~35
-    iterations, so that case is held to 2e-9, a fifth of its solve tolerance."""
+    1e-10 and the iteration counts to 1; at 10^4 contrast the amplification
+    reaches a few 1e-10 after ~35 iterations and the residual history is flat
+    near the tolerance (a ratio of ~0.7 per iteration), so that case is held to
+    2e-9 (a fifth of its solve tolerance) and iteration counts within 2."""
     dims, k, f, spec = mi.workload(name, n)
     O = oracle.Oracle(k)
     xo, ito, info = O.pcg(f, spec["rtol"], maxit=2000)
     import paper_1604_07163_gb300 as mg
     S = mg.MGSolver(T(k), mg.Params(maxit=2000))
     x, st = S.solve(T(f), spec["rtol"])
-    assert abs(st.iters - ito) <= 1, (st.iters, ito)
+    assert abs(st.iters - ito) <= dit, (st.iters, ito)
     assert st.true_rel_resid <= spec["rtol"] * 1.01
     xg = N(x)
     if st.iters == ito:
@@ -163,7 +166,7 @@ def test_telescoping_graph_and_kernel_choice_do_not_change_the_result(gpu_lib):
     dims, k, f, spec = mi.workload("poisson33_fp64", 65)
     ref = None
     for tele, graph, kern, pdl in [(0, 0, 1, 0), (4096, 1, 0, 1), (40000, 1, 2, 1), (10 ** 6, 0, 0, 1),
-                                   (4096, 1, 2, 0)]:
+                                   (4096, 1, 2, 0), (4096, 1, 3, 1)]:
         x, st = mg.MGSolver(T(k), mg.Params(telescope_max_n=tele, use_graph=graph, stencil_kernel=kern,
                                             use_pdl=pdl)).solve(T(f), 1e-10)
         if ref is None:
@@ -194,7 +197,7 @@ def test_mixed_precision_reaches_fp64_tolerance(gpu_lib, precision):
     assert st.iters <= ito + 6
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("precision,tol", [("mixed_fp32", 2e-6), ("mixed_bf16k", 2e-2)])
 def test_mixed_step_parity(gpu_lib, precision, tol, kernel):
     """float32 vectors: rounding of order 1e-7 relative per step; bfloat16
