@@ -80,10 +80,11 @@ typedef struct {
   int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
   int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
   int stencil_kernel;  /* smoother/residual kernels on the levels above the single-block bottom:
-                          0 (default) z-marching with neighbours read through L1, and on levels with
-                            at least 64 points per axis the coarse-grid correction folded into the
-                            first post-smoothing step (shared-plane z-marching kernel),
-                          1 z-marching through L1 only,
+                          0 (default) z-marching 32x4 tiles with neighbours read through L1 (the
+                            fastest measured on GB300),
+                          1 as 0, plus the coarse-grid correction folded into the first
+                            post-smoothing step (shared-plane z-marching kernel) on levels with at
+                            least 64 points per axis,
                           2 TMA-staged tiles (cp.async.bulk.tensor),
                           3 shared-plane z-marching for every pass */
   int use_pdl;         /* 1: launch solve kernels as programmatic dependent launches (default 1) */

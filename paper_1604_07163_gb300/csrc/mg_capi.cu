@@ -269,15 +269,13 @@ void tm_collect(mg_handle* h) {
   h->ev_next = h->ev_graph_end;
 }
 
-// z-marching launch geometry: 32x8 column tiles, planes split so that the
-// grid holds about 8 blocks per SM (levels too small for that get fewer blocks).
+// z-marching launch geometry: 32x4 column tiles; the planes are split into
+// chunks of at least 2 with the best wave efficiency over 8 resident blocks
+// per SM (small levels simply get fewer blocks).
 dim3 zm_grid(const mg_handle* h, const Geom& g, int* kchunk) {
   dim3 grid((g.nx + ZM_TX - 1) / ZM_TX, (g.ny + ZM_TY - 1) / ZM_TY, 1);
-  const int per = grid.x * grid.y;
-  const int target = h->nsm * 8;
-  int zs = (target + per - 1) / per;
-  zs = zs < 1 ? 1 : (zs > g.nz ? g.nz : zs);
-  int kc = (g.nz + zs - 1) / zs;
+  const int zs = best_zsplit(grid.x * grid.y, h->nsm * 8, g.nz, 2);
+  const int kc = (g.nz + zs - 1) / zs;
   grid.z = (g.nz + kc - 1) / kc;
   *kchunk = kc;
   return grid;
@@ -874,7 +872,7 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   if (!mixed) h->lv[0].b = h->cr;  // the V-cycle's finest right-hand side is the CG residual
   // TMA-staged stencil kernels on the levels above the bottom kernel
   for (int l = 0; l < h->lb; ++l) {
-    if (p.stencil_kernel == 0 || p.stencil_kernel == 3) {
+    if (p.stencil_kernel == 1 || p.stencil_kernel == 3) {
       dispatch(h, [&](auto impl) {
         decltype(impl)::zs_prepare(h, l);
         return 0;
@@ -1001,16 +999,14 @@ struct Guard {
 
 template <class I, bool FLEX, class TV>
 mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
-  // p = z + beta p;  q = A p, p.q -> alpha;  x += alpha p, r -= alpha q, r.r (and r.z_old)
-  linear<false>(h, g.len, LinPUpd<TV>{z, h->cp, h->dsc, 0.0}, MG_K_CG_DIR);
+  // x += alpha_prev p, p = z + beta p;  q = A p, p.q -> alpha;  r -= alpha q, r.r (and r.z_old)
+  linear<false>(h, g.len, LinPUpd<TV>{z, h->cp, h->cx, h->dsc, 0.0, 0.0}, MG_K_CG_DIR);
   int nb = zmarch<true>(h, g, OpApplyPQ{h->cp, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64}, MG_K_CG_APPLY, 0);
   finish(h, nb, FIN_PQ);
   if (h->prm.precision == MG_FP64)
-    nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, false>{h->cx, h->cr, h->cp, h->cq, z, nullptr, h->dsc, 0.0},
-                      MG_K_CG_UPD);
+    nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, false>{h->cr, h->cq, z, nullptr, h->dsc, 0.0}, MG_K_CG_UPD);
   else
-    nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, true>{h->cx, h->cr, h->cp, h->cq, z, (float*)L0.b, h->dsc, 0.0},
-                      MG_K_CG_UPD);
+    nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, true>{h->cr, h->cq, z, (float*)L0.b, h->dsc, 0.0}, MG_K_CG_UPD);
   finish(h, nb, FIN_RR);
   return MG_OK;
 }
@@ -1078,6 +1074,8 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
       if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
     }
     if (it > p.maxit) it = p.maxit;
+    // the last iteration's x += alpha p (deferred updates stop at exit)
+    linear<false>(h, g.len, LinXUpd{h->cx, h->cp, h->dsc, 0.0}, MG_K_CG_DIR);
   }
   if ((s = unpack_level(h, 0, h->cx, x, true)) != MG_OK) return s;
   // true residual in float64

@@ -97,6 +97,16 @@ __device__ __forceinline__ R stencil(const Geom& g, int p, const U& u, const TC*
   return S;
 }
 
+// D^-1 at a point: in float32 it is recomputed from the six coefficients the
+// stencil already loaded (the same sum and division that produced the stored
+// inverse, so the value is identical and 4 bytes per point are not read); in
+// float64, where the float64 pipe is the bottleneck, the stored inverse is read.
+template <bool NC, class R, class TV>
+__device__ __forceinline__ R inv_diag(R D, const TV* dinv_p) {
+  if constexpr (sizeof(R) == 4) return (R)1 / D;
+  else return cvt<R>(ldp<NC>(dinv_p));
+}
+
 // ------------------------------------------------------------ point operations
 // Every op exposes  template<bool NC> void pt(g, i, j, k, p, acc0, acc1)
 // and  prepare()  (called once per thread before the point loop).
@@ -137,7 +147,7 @@ template <class R, class TV, class TC> struct OpChebStep {
     LdVec<NC, R, TV> lx{x};
     R S = stencil<NC, R>(g, p, lx, kx, ky, kz, D);
     const R xp = lx(p);
-    const R s = fma(cvt<R>(ldp<NC>(dinv + p)), cvt<R>(ldp<NC>(b + p)) + S, -xp);
+    const R s = fma(inv_diag<NC>(D, dinv + p), cvt<R>(ldp<NC>(b + p)) + S, -xp);
     const R dn = dprev ? fma(c1, cvt<R>(ldp<NC>(dprev + p)), c2 * s) : s * inv_theta;
     const R xn = xp + dn;
     xout[p] = store_as<TV>(xn);
@@ -307,29 +317,54 @@ __device__ __forceinline__ void st4(float* p, const double v[4]) {
   reinterpret_cast<float4*>(p)[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
 }
 
-// p = z + beta p
+// x += alpha p (the update of the previous iteration, deferred to this pass,
+// which reads p anyway), then p = z + beta p.  alpha = 0 on the first iteration.
 template <class TZ> struct LinPUpd {
   const TZ* z;
   double* p;
+  double* x;
   const Scal* sc;
-  double beta;
-  __device__ void prepare() { beta = sc->beta; }
+  double alpha, beta;
+  __device__ void prepare() {
+    alpha = sc->alpha;
+    beta = sc->beta;
+  }
   __device__ __forceinline__ void pt4(i64 t, double&, double&) const {
-    double zv[4], pv[4];
+    double zv[4], pv[4], xv[4];
     ld4(z + t, zv);
     ld4(p + t, pv);
+    ld4(x + t, xv);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) pv[u] = fma(beta, pv[u], zv[u]);
+    for (int u = 0; u < 4; ++u) {
+      xv[u] = fma(alpha, pv[u], xv[u]);
+      pv[u] = fma(beta, pv[u], zv[u]);
+    }
+    st4(x + t, xv);
     st4(p + t, pv);
   }
 };
 
-// x += alpha p, r -= alpha q, acc0 += r.r, acc1 += r.z_old (FLEX); with B32
-// also b32 = (float) r, the float32 right-hand side of the next V-cycle.
-template <class TZ, bool FLEX, bool B32> struct LinCgUpd {
+// x += alpha p (the last iteration's update at exit)
+struct LinXUpd {
   double* x;
-  double* r;
   const double* p;
+  const Scal* sc;
+  double alpha;
+  __device__ void prepare() { alpha = sc->alpha; }
+  __device__ __forceinline__ void pt4(i64 t, double&, double&) const {
+    double xv[4], pv[4];
+    ld4(x + t, xv);
+    ld4(p + t, pv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = fma(alpha, pv[u], xv[u]);
+    st4(x + t, xv);
+  }
+};
+
+// r -= alpha q, acc0 += r.r, acc1 += r.z_old (FLEX); with B32 also
+// b32 = (float) r, the float32 right-hand side of the next V-cycle.
+template <class TZ, bool FLEX, bool B32> struct LinCgUpd {
+  double* r;
   const double* q;
   const TZ* z;
   float* b32;
@@ -337,14 +372,11 @@ template <class TZ, bool FLEX, bool B32> struct LinCgUpd {
   double alpha;
   __device__ void prepare() { alpha = sc->alpha; }
   __device__ __forceinline__ void pt4(i64 t, double& a0, double& a1) const {
-    double xv[4], rv[4], pv[4], qv[4];
-    ld4(x + t, xv);
+    double rv[4], qv[4];
     ld4(r + t, rv);
-    ld4(p + t, pv);
     ld4(q + t, qv);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      xv[u] = fma(alpha, pv[u], xv[u]);
       rv[u] = fma(-alpha, qv[u], rv[u]);
       a0 = fma(rv[u], rv[u], a0);
     }
@@ -354,7 +386,6 @@ template <class TZ, bool FLEX, bool B32> struct LinCgUpd {
 #pragma unroll
       for (int u = 0; u < 4; ++u) a1 = fma(rv[u], zv[u], a1);
     }
-    st4(x + t, xv);
     st4(r + t, rv);
     if constexpr (B32) st4(b32 + t, rv);
   }

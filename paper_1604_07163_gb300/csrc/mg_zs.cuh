@@ -168,13 +168,14 @@ template <class R_, class TV, class TC_, bool kDot_> struct PolStep {
   __device__ __forceinline__ Ctr load_ctr(int p) const {
     Ctr c;
     c.b = __ldg(b + p);
-    c.dinv = __ldg(dinv + p);
+    c.dinv = sizeof(R) == 4 ? store_as<TV>(0.0) : __ldg(dinv + p);
     c.d = dprev ? __ldg(dprev + p) : store_as<TV>(0.0);
     c.r = kDot ? __ldg(r64 + p) : 0.0;
     return c;
   }
-  __device__ __forceinline__ void out(R u, R S, R, const Ctr& c, int p, double& acc) const {
-    const R s = fma(cvt<R>(c.dinv), cvt<R>(c.b) + S, -u);
+  __device__ __forceinline__ void out(R u, R S, R D, const Ctr& c, int p, double& acc) const {
+    const R dv = sizeof(R) == 4 ? (R)1 / D : cvt<R>(c.dinv);
+    const R s = fma(dv, cvt<R>(c.b) + S, -u);
     const R dn = dprev ? fma(c1, cvt<R>(c.d), c2 * s) : s * inv_theta;
     const TV xn = store_as<TV>(u + dn);
     xout[p] = xn;
@@ -227,9 +228,12 @@ template <class R_, class TV, class TC_> struct PolProlongStep0 {
     s += cvt<R>(r.e[6]) + cvt<R>(r.e[7]);
     return fma((R)0.125, s, cvt<R>(r.x));
   }
-  __device__ __forceinline__ Ctr load_ctr(int p) const { return {__ldg(b + p), __ldg(dinv + p)}; }
-  __device__ __forceinline__ void out(R u, R S, R, const Ctr& c, int p, double&) const {
-    const R s = fma(cvt<R>(c.dinv), cvt<R>(c.b) + S, -u);
+  __device__ __forceinline__ Ctr load_ctr(int p) const {
+    return {__ldg(b + p), sizeof(R) == 4 ? store_as<TV>(0.0) : __ldg(dinv + p)};
+  }
+  __device__ __forceinline__ void out(R u, R S, R D, const Ctr& c, int p, double&) const {
+    const R dv = sizeof(R) == 4 ? (R)1 / D : cvt<R>(c.dinv);
+    const R s = fma(dv, cvt<R>(c.b) + S, -u);
     const R dn = s * inv_theta;
     xout[p] = store_as<TV>(u + dn);
     if (dout) dout[p] = store_as<TV>(dn);

@@ -59,9 +59,9 @@ def make(dims, block, rng, params, seed=101):
 @pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_step_parity_fp64(gpu_lib, case, kernel):
-    """kernel 0: default (L1 z-marching, prolongation folded into the first
-    post-smoothing step on large levels); 1: L1 z-marching only; 2: TMA-staged
-    tiles; 3: shared-plane z-marching for every pass."""
+    """kernel 0: default L1 z-marching; 1: plus prolongation folded into the
+    first post-smoothing step on large levels; 2: TMA-staged tiles;
+    3: shared-plane z-marching for every pass."""
     dims, block, rng, params = CASES[case]
     k, O, S = make(dims, block, rng, dict(params, stencil_kernel=kernel))
     for l in range(O.levels):
@@ -83,6 +83,23 @@ def test_step_parity_fp64(gpu_lib, case, kernel):
     # the float64 outer operator
     x = mi.random_nodal(dims, 60)
     assert relmax(N(S.apply(T(x), -1)), O.apply(x)) < 1e-13
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+def test_vcycle_parity_large_levels(gpu_lib, kernel):
+    """129^3: levels with >= 64 points per axis, where kernel 1 folds the
+    coarse-grid correction into the first post-smoothing step; also the
+    float32 V-cycle of the same hierarchy."""
+    import paper_1604_07163_gb300 as mg
+    dims = (129, 129, 129)
+    k = mi.cell_k(dims, 8, -2.0, 2.0, 55)
+    O = oracle.Oracle(k)
+    r = mi.random_nodal(dims, 56)
+    zo = O.vcycle(r)
+    S = mg.MGSolver(T(k), mg.Params(stencil_kernel=kernel))
+    assert relmax(N(S.vcycle(T(r))), zo) < 1e-12
+    S32 = mg.MGSolver(T(k), mg.Params(stencil_kernel=kernel, precision="mixed_fp32"))
+    assert relmax(N(S32.vcycle(T(r))), zo) < 1e-5
 
 
 def test_boundary_entries_ignored_and_zeroed(gpu_lib):
