@@ -76,7 +76,7 @@ typedef struct {
   mg_precision precision;
   int maxit;           /* CG iteration limit (default 1000) */
   int nonzero_guess;   /* 1: mg_solve starts from the x passed in */
-  int flexible;        /* CG beta: 0 Fletcher-Reeves, 1 Polak-Ribiere (flexible); -1 = 0 for FP64, 1 for mixed */
+  int flexible;        /* CG beta: 0 Fletcher-Reeves, 1 Polak-Ribiere (flexible); -1 (default) = 0 */
   int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
   int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
   int stencil_kernel;  /* smoother/residual kernels on the levels above the single-block bottom:

@@ -1134,7 +1134,10 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
       p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 3)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
-  if (p.flexible < 0) p.flexible = p.precision == MG_FP64 ? 0 : 1;
+  // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
+  // V-cycles need the same iteration counts with it as with the flexible
+  // (Polak-Ribiere) beta, which costs one more dot product per iteration.
+  if (p.flexible < 0) p.flexible = 0;
   mg_handle* h = new (std::nothrow) mg_handle();
   if (!h) return fail(nullptr, MG_ERR_ALLOC, "host allocation failed");
   h->prm = p;

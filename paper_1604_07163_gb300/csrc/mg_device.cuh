@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace mgdev {
 
@@ -37,6 +38,76 @@ struct Geom {
 };
 
 // ------------------------------------------------------------ conversions
+// float <-> double conversions on the integer pipe.  On GB300 the float64 pipe
+// (which also executes F2F conversions) is the scarce unit of the outer CG, so
+// the float32 vectors that meet float64 ones there are converted with bit
+// operations instead:
+//   f2d_bits: exact for zeros, normal numbers, infinities and NaNs; a
+//             subnormal float becomes a signed zero;
+//   d2f_bits: round to nearest, ties to even, exactly as a float64 -> float32
+//             conversion for every result in the normal float range; results
+//             below it become a signed zero, above it infinity.
+__host__ __device__ __forceinline__ unsigned long long dbits(double d) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(d);
+#else
+  unsigned long long u;
+  memcpy(&u, &d, 8);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double bitsd(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double d;
+  memcpy(&d, &u, 8);
+  return d;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned fbits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ float bitsf(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = fbits(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long mant = e == 0 ? 0ull : (unsigned long long)(u & 0x7fffffu) << 29;
+  const unsigned long long E = e == 0 ? 0ull : (e == 255 ? 2047ull : (unsigned long long)(e + 896u));
+  return bitsd(sign | (E << 52) | mant);
+}
+__host__ __device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned long long u = dbits(d);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned long long m = u & 0xfffffffffffffull;
+  if (e == 0x7ff) return bitsf(sign | 0x7f800000u | (m ? 0x400000u : 0u));  // infinity, NaN
+  const int fe = e - 1023 + 127;
+  if (fe >= 255) return bitsf(sign | 0x7f800000u);
+  if (fe <= 0) return bitsf(sign);
+  unsigned keep = (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1fffffffull;
+  if (rem > 0x10000000ull || (rem == 0x10000000ull && (keep & 1u))) ++keep;
+  const unsigned bits = ((unsigned)fe << 23) + keep;  // a mantissa carry moves into the exponent
+  if ((bits >> 23) >= 255u) return bitsf(sign | 0x7f800000u);
+  return bitsf(sign | bits);
+}
+
 template <class R> __device__ __forceinline__ R cvt(double v) { return (R)v; }
 template <class R> __device__ __forceinline__ R cvt(float v) { return (R)v; }
 template <class R> __device__ __forceinline__ R cvt(__nv_bfloat16 v) { return (R)__bfloat162float(v); }
@@ -296,6 +367,9 @@ struct OpApplyPQ {
   }
 };
 
+__device__ __forceinline__ double to_double(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+
 // ---- linear (pointwise) kernels over whole padded arrays ---------------------
 // Pad slots hold zeros in every vector and stay zero under these updates, so
 // the pointwise CG kernels run over [0, len) with 4 consecutive elements per
@@ -307,14 +381,14 @@ __device__ __forceinline__ void ld4(const double* p, double v[4]) {
 }
 __device__ __forceinline__ void ld4(const float* p, double v[4]) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[0] = f2d_bits(a.x); v[1] = f2d_bits(a.y); v[2] = f2d_bits(a.z); v[3] = f2d_bits(a.w);
 }
 __device__ __forceinline__ void st4(double* p, const double v[4]) {
   reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 __device__ __forceinline__ void st4(float* p, const double v[4]) {
-  reinterpret_cast<float4*>(p)[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  reinterpret_cast<float4*>(p)[0] = make_float4(d2f_bits(v[0]), d2f_bits(v[1]), d2f_bits(v[2]), d2f_bits(v[3]));
 }
 
 // x += alpha p (the update of the previous iteration, deferred to this pass,
@@ -415,7 +489,7 @@ template <class R, class TV, class TC> struct OpChebStepDot {
   template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double& a0,
                                                         double&) const {
     const R xn = step.template step<NC>(g, p);
-    a0 = fma(ldp<NC>(r + p), (double)store_as<TV>(xn), a0);
+    a0 = fma(ldp<NC>(r + p), to_double(store_as<TV>(xn)), a0);
   }
 };
 

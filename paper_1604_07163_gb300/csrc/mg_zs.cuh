@@ -180,7 +180,7 @@ template <class R_, class TV, class TC_, bool kDot_> struct PolStep {
     const TV xn = store_as<TV>(u + dn);
     xout[p] = xn;
     if (dout) dout[p] = store_as<TV>(dn);
-    if constexpr (kDot) acc = fma(c.r, cvt<double>(xn), acc);
+    if constexpr (kDot) acc = fma(c.r, to_double(xn), acc);
   }
 };
 
