@@ -34,19 +34,23 @@ HEADLINE = "mixed_fp32"
 FORMS = ("mixed_fp32", "fp64", "mixed_bf16k")
 
 # Algorithmic HBM bytes per interior point for one launch of each kernel class,
-# as a function of the vector element size v, the three-coefficient bytes c and
-# the inverse-diagonal bytes v.  (Re-reads of neighbours served from cache are
-# not counted: each array is read once per point.)
-def bytes_per_point(cls: str, v: int, c: int, degree: int = 2) -> float:
+# as a function of the vector element size v and the three-coefficient bytes c
+# (each array counted once per point: neighbour re-reads served from cache are
+# not).  float32 smoothers recompute D^-1 from the six coefficients; the float64
+# ones read it (dinv = v).  The finest level's post-smoothing is step 0 (reads
+# x, b; writes x, d) and step 1 with rho = r.z fused (reads x, d, b, float64 r;
+# writes z): cheb_step is their average.
+def bytes_per_point(cls: str, v: int, c: int, degree: int = 2, fp64: bool = False, flexible: bool = False) -> float:
+    dinv = v if fp64 else 0
     return {
         "cheb_zero": 3 * v + c + (v if degree > 2 else 0),  # read b, dinv, k; write x (and d)
-        "cheb_step": 5 * v + c,                           # read x, d|-, b, dinv, k; write x, d|-
+        "cheb_step": 4 * v + c + 4 + dinv,                # (x+b+k+x'+d) and (x+d+b+k+z+r64), averaged
         "resid": 3 * v + c,                               # read x, b, k; write r
         "restrict": 9 * v,                                # per coarse point: read 8 fine r, write 1
         "prolong": 2 * v + v / 8,                         # read x, e/8; write x
-        "cg_dir": 16 + v,                                 # read z, p; write p (float64 p)
-        "cg_apply": 4 * 8 + 24,                           # read p, D, k64; write q (float64)
-        "cg_upd": 6 * 8 + v,                              # read x, r, p, q, z; write x, r
+        "cg_dir": 32 + v,                                 # read z, p, x; write p, x (float64 p, x)
+        "cg_apply": 3 * 8 + 24,                           # read p, D, k64; write q (float64)
+        "cg_upd": 24 + (0 if fp64 else 4) + (v if flexible else 0),  # read r, q (z); write r (, float32 b)
         "dot": 8 + v,                                     # read r (float64), z
         "cast": 12,                                       # float64 r -> float32 b
     }[cls]
@@ -240,7 +244,7 @@ def run_ours(args):
 
     forms = {}
     solutions = {}
-    roofline = clocks = None
+    roofline = smoother = clocks = None
     launches = 0
     run_forms = [HEADLINE] + [fm for fm in args.forms.split(",") if fm in FORMS and fm != HEADLINE]
     def step(S):
@@ -291,9 +295,10 @@ def run_ours(args):
         solutions[form] = x.detach().clone()
         if headline:
             # the same K steps again with CUDA events around every launch of the
-            # dominant finest-level kernel class (events inside the V-cycle graph
-            # slow the whole solve, so the headline steps above run without them)
-            S.timing(True, classes=[dom], levels=[0])
+            # dominant finest-level kernel class and of the smoother steps (events
+            # inside the V-cycle graph slow the whole solve, so the headline steps
+            # above run without them)
+            S.timing(True, classes=[dom] if dom == "cheb_step" else [dom, "cheb_step"], levels=[0])
             for _ in range(args.steps):
                 S.solve(f, rtol, raise_on_error=False)
             torch.cuda.synchronize()
@@ -301,7 +306,8 @@ def run_ours(args):
             launches = launches_form
             kt = S.kernel_times()
             S.timing(False)
-            roofline = roofline_from(kt, form, clocks)
+            roofline = roofline_from(kt, form, clocks, dom, args.workload)
+            smoother = roofline_from(kt, form, clocks, "cheb_step", args.workload)
             forms[form]["kernel_ms_per_solve_warmup_profile"] = {f"{c}@L{l}": round(v[0], 4)
                                                                   for (c, l), v in profile_all.items()}
             # end to end: pinned host f -> device, solve, x -> pinned host, every step
@@ -347,7 +353,7 @@ def run_ours(args):
         "data": "synthetic", "config": config_dict(spec, world, forms[HEADLINE]["iters"], args.workload,
                                                    args.face_rule, args.adjoint),
         "forms": forms, "speedup_mixed_vs_fp64": speedup,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        "roofline": roofline, "smoother_roofline": smoother, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -360,23 +366,43 @@ CG_APPLY_FLOPS = 16
 # GB300: 152 SMs x 2 float64 FMA per clock per SM (the nominal 1.25 TFLOP/s at 2.07 GHz)
 FP64_FLOP_PER_SM_CLK = 4
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# finest-level kernel classes, from one ncu capture each on the 257^3 workload
+# (profiles/ holds the summaries), keyed by the hash of the CUDA sources they
+# were captured with: once the sources change the figure no longer describes
+# the kernel and traffic is reported as null.
+NCU_TRAFFIC = {}
 
-def roofline_from(kt, form, clocks):
-    """Dominant level-0 kernel of the timed region: algorithmic GB/s vs the
-    measured HBM peak, or float64 FLOP/s vs the float64 pipe peak for the
-    float64-pipe-bound outer-CG operator."""
-    v, c = form_sizes(form)
-    peak, which = load_peaks()
-    best = None
-    for (cls, lvl), (ms, nl, pts) in kt.items():
-        if lvl != 0 or cls in ("bottom",):
-            continue
-        if best is None or ms > best[1]:
-            best = (cls, ms, nl, pts)
-    if best is None:
+
+def csrc_hash() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_1604_07163_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(fn.encode())
+            with open(os.path.join(d, fn), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, form, cls):
+    rec = NCU_TRAFFIC.get((workload, form, cls))
+    if rec is None or rec[1] != csrc_hash():
         return None
-    cls, ms, nl, pts = best
+    return rec[0]
+
+
+def roofline_from(kt, form, clocks, cls, workload):
+    """Roofline entry of level-0 kernel class cls from the live CUDA-event
+    timing: algorithmic GB/s vs the measured HBM peak, or float64 FLOP/s vs
+    the float64 pipe peak for the float64-pipe-bound outer-CG operator."""
+    rec = kt.get((cls, 0))
+    if rec is None:
+        return None
+    ms, nl, pts = rec
     avg_s = ms * 1e-3 / nl
+    traffic = measured_traffic(workload, form, cls)
     if cls == "cg_apply":
         mhz = clocks["sm_mhz"] if clocks else 2070.0
         fpeak = 152 * FP64_FLOP_PER_SM_CLK * mhz * 1e6 / 1e12
@@ -384,15 +410,15 @@ def roofline_from(kt, form, clocks):
         ach = flops / avg_s / 1e12
         return {"bound": "alu", "kernel": cls, "achieved": ach, "peak": fpeak, "unit": "TFLOP/s",
                 "frac": ach / fpeak, "peak_source": "derived: 152 SMs x 4 float64 flop/clk x median SM clock",
-                "traffic": None, "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms / nl, "launches": nl}
-    bpp = bytes_per_point(cls, v, c)
-    if cls == "restrict":
-        bpp = 9 * v  # points counted on the coarse grid
-    traffic = bpp * pts / nl
-    achieved = traffic / avg_s / 1e9
+                "traffic": traffic, "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms / nl, "launches": nl}
+    v, c = form_sizes(form)
+    peak, which = load_peaks()
+    bpp = bytes_per_point(cls, v, c, fp64=form == "fp64")
+    alg = bpp * pts / nl  # restrict: pts are coarse points
+    achieved = alg / avg_s / 1e9
     return {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": which, "traffic": None,
-            "algorithmic_bytes_per_launch": traffic, "avg_launch_ms": ms / nl, "launches": nl}
+            "frac": achieved / peak, "peak_source": which, "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms / nl, "launches": nl}
 
 
 def main():

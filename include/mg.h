@@ -64,10 +64,16 @@ typedef enum {
   MG_MIXED_BF16K = 2  /* V-cycle in float32 with bfloat16 edge coefficients inside float64 CG */
 } mg_precision;
 
+typedef enum {
+  MG_SMOOTHER_CHEBYSHEV = 0,  /* Chebyshev(cheby_degree) preconditioned with Jacobi (Sec. 4.3) */
+  MG_SMOOTHER_RICHARDSON = 1  /* Richardson preconditioned with Jacobi, x += omega D^-1 (b - A x)
+                                 (Sec. 2.1.1; Sec. 5 runs eight iterations per level) */
+} mg_smoother;
+
 typedef struct {
   int levels;          /* number of levels; 0 = coarsen until an axis has 3 interior points */
   int nu_pre, nu_post; /* smoother sweeps before / after the coarse correction (default 1, 1) */
-  int cheby_degree;    /* Chebyshev iterations per sweep (default 2: "V(2,2), Chebyshev(2)") */
+  int cheby_degree;    /* Chebyshev iterations per sweep, 1..32 (default 2: "V(2,2), Chebyshev(2)") */
   double eig_lo_frac;  /* interval [eig_lo_frac*eig_hi, eig_hi] for D^-1 A (default 0.1) */
   double eig_hi;       /* upper end; 2.0 bounds the spectrum of D^-1 A (Gershgorin) */
   int coarse_k_rule;   /* coarse cell k from its 8 children: 0 arithmetic (default), 1 geometric, 2 harmonic mean */
@@ -80,14 +86,22 @@ typedef struct {
   int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
   int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
   int stencil_kernel;  /* smoother/residual kernels on the levels above the single-block bottom:
-                          0 (default) z-marching 32x4 tiles with neighbours read through L1 (the
-                            fastest measured on GB300),
+                          0 (default) z-marching, 64x4 tiles of two consecutive points per
+                            thread: vector loads, x neighbours by warp shuffles, z neighbours
+                            in registers, L2 prefetch two planes ahead (the fastest measured
+                            on GB300),
                           1 as 0, plus the coarse-grid correction folded into the first
                             post-smoothing step (shared-plane z-marching kernel) on levels with at
                             least 64 points per axis,
                           2 TMA-staged tiles (cp.async.bulk.tensor),
-                          3 shared-plane z-marching for every pass */
+                          3 shared-plane z-marching for every pass,
+                          4 z-marching with one point per thread and neighbours read through L1 */
   int use_pdl;         /* 1: launch solve kernels as programmatic dependent launches (default 1) */
+  int smoother;        /* mg_smoother (default MG_SMOOTHER_CHEBYSHEV).  With Richardson, nu_pre and
+                          nu_post count iterations and cheby_degree, eig_lo_frac, eig_hi are unused */
+  double richardson_omega; /* Richardson damping, > 0.  The paper gives none; the default 6/7 is
+                              the weight that minimises Jacobi's smoothing factor for the 7-point
+                              operator (1.0 leaves the highest modes undamped) */
 } mg_params;
 
 typedef struct {

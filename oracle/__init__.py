@@ -8,7 +8,8 @@ including the zero Dirichlet boundary.
 
 The functions follow these passages of the paper: Eq. 1-2 (operator),
 Algorithm 1 applied recursively (V-cycle), Sec. 2.1.1 (level components),
-Sec. 4.3 (Chebyshev smoother preconditioned with Jacobi), Sec. 1 and
+Sec. 4.3 (Chebyshev smoother preconditioned with Jacobi; Richardson-Jacobi,
+Sec. 2.1.1 and Sec. 5), Sec. 1 and
 Sec. 3.3.1 (exact coarse factorisation), Sec. 2.1 / 4.2 (CG with a relative
 residual stopping test).  The gradient (adjoint) is not in the paper; it is
 the standard discrete adjoint of the same operator.
@@ -48,6 +49,11 @@ def _load():
         lib.orc_create.restype = vp
         lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, _dptr, C.c_int, C.c_int, C.c_int,
                                    C.c_int, C.c_double, C.c_double, C.c_int, C.c_int]
+        lib.orc_create_opt.restype = vp
+        lib.orc_create_opt.argtypes = [C.c_int, C.c_int, C.c_int, _dptr, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]
+        lib.orc_level_beta.restype = C.c_double
+        lib.orc_level_beta.argtypes = [vp, C.c_int]
         lib.orc_free.argtypes = [vp]
         lib.orc_num_levels.argtypes = [vp]
         lib.orc_level_dims.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
@@ -66,6 +72,8 @@ def _load():
         lib.orc_pcg.restype = C.c_int
         lib.orc_pcg.argtypes = [vp, _dptr, _dptr, C.c_double, C.c_int, C.c_int, C.c_int, vp, _dptr]
         lib.orc_gradient.argtypes = [vp, _dptr, _dptr, _dptr]
+        lib.orc_set_smoother.restype = C.c_int
+        lib.orc_set_smoother.argtypes = [vp, C.c_int, C.c_double]
         _lib = lib
     return _lib
 
@@ -85,22 +93,32 @@ class Oracle:
 
     def __init__(self, k_cells, levels: int | None = None, nu_pre: int = 1, nu_post: int = 1,
                  degree: int = 2, eig_lo_frac: float = 0.1, eig_hi: float = 2.0,
-                 coarse_rule: int = 0, face_rule: int = 0):
+                 coarse_rule: int = 0, face_rule: int = 0, smoother: int = 0, omega: float = 6.0 / 7.0,
+                 galerkin: bool = False):
+        """smoother 0: Chebyshev(degree)-Jacobi sweeps; 1: Richardson-Jacobi
+        iterations x += omega D^-1 (b - A x), nu_pre / nu_post of them.
+        galerkin: coarse operators R A P instead of re-discretisation."""
         lib = _load()
         k = np.ascontiguousarray(k_cells, dtype=np.float64)
         self.dims = tuple(s + 1 for s in k.shape)
         self.levels = levels if levels is not None else default_levels(self.dims)
         nz, ny, nx = self.dims
-        self._h = lib.orc_create(nx, ny, nz, k, self.levels, nu_pre, nu_post, degree, eig_lo_frac,
-                                  eig_hi, coarse_rule, face_rule)
+        self._h = lib.orc_create_opt(nx, ny, nz, k, self.levels, nu_pre, nu_post, degree, eig_lo_frac,
+                                      eig_hi, coarse_rule, face_rule, 1 if galerkin else 0)
         if not self._h:
             raise ValueError("oracle: invalid grid, levels or k field")
         self._lib = lib
+        if lib.orc_set_smoother(self._h, smoother, omega) != 0:
+            raise ValueError("oracle: invalid smoother")
 
     def __del__(self):
         if getattr(self, "_h", None):
             self._lib.orc_free(self._h)
             self._h = None
+
+    def level_beta(self, l: int) -> float:
+        """Upper end of level l's Chebyshev interval."""
+        return self._lib.orc_level_beta(self._h, l)
 
     def level_dims(self, l: int):
         N = (C.c_int * 3)()

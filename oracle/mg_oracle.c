@@ -55,6 +55,7 @@ typedef struct {
   double *diag;
   double *b, *x, *r, *s, *d, *t; /* work vectors (interior numbering) */
   int face_rule;
+  double alpha, beta;  /* Chebyshev interval for D^-1 A on this level */
 } olevel;
 
 typedef struct {
@@ -62,9 +63,12 @@ typedef struct {
   olevel lv[ORC_MAX_LEVELS];
   int nu_pre, nu_post, degree;
   double alpha, beta;  /* Chebyshev interval for D^-1 A */
+  int smoother;        /* 0 Chebyshev-Jacobi, 1 Richardson-Jacobi */
+  double omega;        /* Richardson damping */
   int nc;              /* unknowns on the coarsest level */
   int coarse_rule;     /* 0 arithmetic, 1 geometric, 2 harmonic mean of children */
   int face_rule;       /* edge k: 0 harmonic, 1 arithmetic mean of the 4 cells */
+  int galerkin;        /* coarse operators: 0 re-discretised, 1 Galerkin R A P */
   double *Ac, *Lc;     /* dense coarsest operator and its Cholesky factor */
 } ohier;
 
@@ -244,6 +248,90 @@ static void prolong_add(const olevel *F, const olevel *C, const double *ec, doub
       }
 }
 
+/* ------------------------------------------------------------ Galerkin */
+/* Galerkin coarse operator A_c = R A_f P with R = P^T / 8 (the paper's runs
+ * use Galerkin coarse operators, Sec. 4.3 and Sec. 5), entry by entry from
+ * the definition (A_c)_IJ = sum_{i,j} R_Ii (A_f)_ij P_jJ: for each coarse row
+ * I, the 27 fine rows i of R's stencil, each stored entry a_ij of fine row i,
+ * and the coarse interior nodes J that interpolate to fine node j.  J - I
+ * lies in {-1,0,1}^3, so rows have at most 27 entries (increasing column
+ * order).  The diagonal is kept in diag. */
+static int galerkin(const olevel *F, olevel *C) {
+  long n = C->n;
+  C->rowptr = (long *)malloc(sizeof(long) * (n + 1));
+  C->col = (int *)malloc(sizeof(int) * n * 27);
+  C->val = (double *)malloc(sizeof(double) * n * 27);
+  C->diag = (double *)malloc(sizeof(double) * n);
+  int *cnt = (int *)malloc(sizeof(int) * n);
+  if (!C->rowptr || !C->col || !C->val || !C->diag || !cnt) {
+    free(cnt);
+    return -1;
+  }
+#pragma omp parallel for schedule(static)
+  for (int ck = 0; ck < C->nz; ++ck)
+    for (int cj = 0; cj < C->ny; ++cj)
+      for (int ci = 0; ci < C->nx; ++ci) {
+        const int I0 = ci + 1, J0 = cj + 1, K0 = ck + 1; /* coarse full coordinates */
+        double acc[27];
+        for (int e = 0; e < 27; ++e) acc[e] = 0.0;
+        for (int c = -1; c <= 1; ++c)
+          for (int b = -1; b <= 1; ++b)
+            for (int a = -1; a <= 1; ++a) {
+              const int fI = 2 * I0 + a, fJ = 2 * J0 + b, fK = 2 * K0 + c; /* fine full coordinates of i */
+              const double rI = pw(fI, I0) * pw(fJ, J0) * pw(fK, K0) / 8.0;
+              const long i = uidx(F, fI - 1, fJ - 1, fK - 1);
+              for (long q = F->rowptr[i]; q < F->rowptr[i + 1]; ++q) {
+                const long jl = F->col[q];
+                const int jI = (int)(jl % F->nx) + 1, jJ = (int)((jl / F->nx) % F->ny) + 1,
+                          jK = (int)(jl / ((long)F->nx * F->ny)) + 1;
+                for (int CK = jK / 2; CK <= (jK + 1) / 2; ++CK)
+                  for (int CJ = jJ / 2; CJ <= (jJ + 1) / 2; ++CJ)
+                    for (int CI = jI / 2; CI <= (jI + 1) / 2; ++CI) {
+                      if (!interior(C, CI, CJ, CK)) continue;
+                      const double pj = pw(jI, CI) * pw(jJ, CJ) * pw(jK, CK);
+                      if (pj == 0.0) continue;
+                      acc[((CK - K0 + 1) * 3 + (CJ - J0 + 1)) * 3 + (CI - I0 + 1)] += rI * F->val[q] * pj;
+                    }
+              }
+            }
+        const long p = uidx(C, ci, cj, ck);
+        long base = p * 27;
+        int m = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (!interior(C, I0 + dx, J0 + dy, K0 + dz)) continue;
+              C->col[base + m] = (int)uidx(C, ci + dx, cj + dy, ck + dz);
+              C->val[base + m] = acc[((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1)];
+              ++m;
+            }
+        cnt[p] = m;
+        C->diag[p] = acc[13];
+      }
+  C->rowptr[0] = 0;
+  for (long p = 0; p < n; ++p) C->rowptr[p + 1] = C->rowptr[p] + cnt[p];
+  for (long p = 0; p < n; ++p) {
+    long src = p * 27, dst = C->rowptr[p];
+    for (int m = 0; m < cnt[p]; ++m) {
+      C->col[dst + m] = C->col[src + m];
+      C->val[dst + m] = C->val[src + m];
+    }
+  }
+  free(cnt);
+  return 0;
+}
+
+/* Gershgorin bound of D^-1 A: max over rows of sum_j |a_ij| / a_ii. */
+static double gershgorin(const olevel *L) {
+  double g = 0.0;
+  for (long p = 0; p < L->n; ++p) {
+    double s = 0.0;
+    for (long q = L->rowptr[p]; q < L->rowptr[p + 1]; ++q) s += fabs(L->val[q]);
+    if (s / L->diag[p] > g) g = s / L->diag[p];
+  }
+  return g;
+}
+
 /* ------------------------------------------------------------ smoother */
 /* One sweep of degree-m Chebyshev iteration for D^-1 A on [alpha, beta]
  * (preconditioned Chebyshev recurrence, Saad, Iterative Methods for Sparse
@@ -252,7 +340,7 @@ static void prolong_add(const olevel *F, const olevel *C, const double *ec, doub
  * m times: x += d and, unless last, s = D^-1(b - A x),
  * rho_j = 1/(2 sigma - rho_{j-1}), d = rho_j rho_{j-1} d + (2 rho_j/delta) s. */
 static void cheby_sweep(const ohier *H, olevel *L, const double *b, double *x, int zero_guess) {
-  const double theta = 0.5 * (H->beta + H->alpha), delta = 0.5 * (H->beta - H->alpha);
+  const double theta = 0.5 * (L->beta + L->alpha), delta = 0.5 * (L->beta - L->alpha);
   const double sigma = theta / delta;
   double rho_prev = 1.0 / sigma;
   long n = L->n;
@@ -282,6 +370,27 @@ static void cheby_sweep(const ohier *H, olevel *L, const double *b, double *x, i
       rho_prev = rho;
     }
   }
+}
+
+/* One Richardson iteration preconditioned with Jacobi, the classical
+ * fixed-point smoother of Sec. 2.1.1 (Sec. 5 runs eight of them per level):
+ * x += omega D^-1 (b - A x).  From a zero guess the residual is b. */
+static void richardson_sweep(const ohier *H, olevel *L, const double *b, double *x, int zero_guess) {
+  const long n = L->n;
+  double *t = L->t;
+  if (zero_guess) {
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < n; ++p) x[p] = H->omega * (b[p] / L->diag[p]);
+    return;
+  }
+  spmv(L, x, t);
+#pragma omp parallel for schedule(static)
+  for (long p = 0; p < n; ++p) x[p] += H->omega * ((b[p] - t[p]) / L->diag[p]);
+}
+
+static void smooth_sweep(const ohier *H, olevel *L, const double *b, double *x, int zero_guess) {
+  if (H->smoother == 1) richardson_sweep(H, L, b, x, zero_guess);
+  else cheby_sweep(H, L, b, x, zero_guess);
 }
 
 /* ------------------------------------------------------------ coarse solve */
@@ -339,23 +448,30 @@ static void vcycle(ohier *H, int l, const double *b, double *x) {
   }
   olevel *C = &H->lv[l + 1];
   memset(x, 0, sizeof(double) * L->n);
-  for (int s = 0; s < H->nu_pre; ++s) cheby_sweep(H, L, b, x, s == 0);
+  for (int s = 0; s < H->nu_pre; ++s) smooth_sweep(H, L, b, x, s == 0);
   spmv(L, x, L->r);
 #pragma omp parallel for schedule(static)
   for (long p = 0; p < L->n; ++p) L->r[p] = b[p] - L->r[p];
   restrict_fw(L, C, L->r, C->b);
   vcycle(H, l + 1, C->b, C->x);
   prolong_add(L, C, C->x, x);
-  for (int s = 0; s < H->nu_post; ++s) cheby_sweep(H, L, b, x, 0);
+  for (int s = 0; s < H->nu_post; ++s) smooth_sweep(H, L, b, x, 0);
 }
 
 /* ------------------------------------------------------------ public API */
 void orc_free(void *hh);
 
-void *orc_create(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pre, int nu_post,
-                 int degree, double eig_lo_frac, double eig_hi, int coarse_rule, int face_rule) {
+/* coarse_op 0: re-discretised coarse operators (cell k averaged by
+ * coarse_rule); 1: Galerkin R A P.  The Chebyshev interval of a level is
+ * [eig_lo_frac beta, beta] with beta = eig_hi on re-discretised levels (their
+ * Gershgorin bound is 2) and the level's Gershgorin bound of D^-1 A on
+ * Galerkin levels. */
+void *orc_create_opt(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pre, int nu_post,
+                     int degree, double eig_lo_frac, double eig_hi, int coarse_rule, int face_rule,
+                     int coarse_op) {
   if (levels < 1 || levels > ORC_MAX_LEVELS || degree < 1 || nu_pre < 0 || nu_post < 0) return NULL;
   if (coarse_rule < 0 || coarse_rule > 2 || face_rule < 0 || face_rule > 1) return NULL;
+  if (coarse_op < 0 || coarse_op > 1) return NULL;
   ohier *H = (ohier *)calloc(1, sizeof(ohier));
   if (!H) return NULL;
   H->L = levels;
@@ -363,9 +479,11 @@ void *orc_create(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pr
   H->nu_post = nu_post;
   H->degree = degree;
   H->beta = eig_hi;
+  H->omega = 6.0 / 7.0;
   H->alpha = eig_lo_frac * eig_hi;
   H->coarse_rule = coarse_rule;
   H->face_rule = face_rule;
+  H->galerkin = coarse_op;
   int N[3] = {Nx, Ny, Nz};
   for (int l = 0; l < levels; ++l) {
     olevel *L = &H->lv[l];
@@ -403,7 +521,14 @@ void *orc_create(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pr
             L->kc[((long)ck * (N[1] - 1) + cj) * (N[0] - 1) + ci] = m;
           }
     }
-    if (assemble(L)) goto fail;
+    if (l > 0 && H->galerkin) {
+      if (galerkin(&H->lv[l - 1], L)) goto fail;
+      L->beta = gershgorin(L);
+    } else {
+      if (assemble(L)) goto fail;
+      L->beta = eig_hi;
+    }
+    L->alpha = eig_lo_frac * L->beta;
     long n = L->n;
     L->b = (double *)calloc(n, sizeof(double));
     L->x = (double *)calloc(n, sizeof(double));
@@ -426,6 +551,15 @@ fail:
   orc_free(H);
   return NULL;
 }
+
+void *orc_create(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pre, int nu_post,
+                 int degree, double eig_lo_frac, double eig_hi, int coarse_rule, int face_rule) {
+  return orc_create_opt(Nx, Ny, Nz, kc, levels, nu_pre, nu_post, degree, eig_lo_frac, eig_hi, coarse_rule,
+                        face_rule, 0);
+}
+
+/* Upper end of level l's Chebyshev interval. */
+double orc_level_beta(void *hh, int l) { return ((ohier *)hh)->lv[l].beta; }
 
 void orc_free(void *hh) {
   ohier *H = (ohier *)hh;
@@ -487,10 +621,20 @@ void orc_smooth(void *hh, int l, const double *bf, double *xf, int zero_guess) {
   double *b = (double *)malloc(sizeof(double) * L->n), *x = (double *)calloc(L->n, sizeof(double));
   to_interior(L, bf, b);
   if (!zero_guess) to_interior(L, xf, x);
-  cheby_sweep(H, L, b, x, zero_guess);
+  smooth_sweep(H, L, b, x, zero_guess);
   to_full(L, x, xf);
   free(b);
   free(x);
+}
+
+/* Smoother choice: 0 Chebyshev-Jacobi (default), 1 Richardson-Jacobi with
+ * damping omega (one iteration per sweep). */
+int orc_set_smoother(void *hh, int smoother, double omega) {
+  ohier *H = (ohier *)hh;
+  if (!H || smoother < 0 || smoother > 1 || !(omega > 0.0)) return -1;
+  H->smoother = smoother;
+  H->omega = omega;
+  return 0;
 }
 
 /* bc = R (b - A x) from level l to level l+1. */

@@ -17,6 +17,7 @@
 #include "mg_kernels.cuh"
 #include "mg_tma.cuh"
 #include "mg_zs.cuh"
+#include "mg_zvec.cuh"
 
 using namespace mgdev;
 
@@ -54,6 +55,7 @@ struct mg_handle {
   int L = 0, lb = 0;  // levels; first level of the bottom kernel
   LevelBuf lv[MG_MAX_LEVELS];
   double* Lc = nullptr;  // Cholesky factor of the coarsest operator
+  double* Li = nullptr;  // its inverse and the transpose when the coarsest level has at most 32 unknowns
   int nc = 0;
   double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cq = nullptr, *cp = nullptr;
   double* cw = nullptr;    // float64 scratch (gradient input)
@@ -70,8 +72,8 @@ struct mg_handle {
   cudaGraphExec_t vexec = nullptr;
   int vexec_zcur = 0;
   bool rz_fused = false;         // last V-cycle fused rho = r.z into its final step
-  int bot_smem_budget = 0;       // dynamic shared memory the bottom kernel may use
-  int lin_grid = 0;              // blocks of the linear (pointwise) kernels
+  bool zvec = true;              // stencil passes on the two-points-per-thread driver (k_zvec)
+  int lin_grid = 0;              // largest grid of the linear (pointwise) kernels
   long long launches = 0;        // kernels launched (counted at launch sites)
   long long graph_launches = 0;  // kernels inside the captured V-cycle graph
   // opt-in kernel timing
@@ -281,9 +283,31 @@ dim3 zm_grid(const mg_handle* h, const Geom& g, int* kchunk) {
   return grid;
 }
 
+dim3 zv_grid(const mg_handle* h, const Geom& g, int* kchunk) {
+  dim3 grid((g.nx + ZV_TX - 1) / ZV_TX, (g.ny + ZV_TY - 1) / ZV_TY, 1);
+  const int zs = best_zsplit(grid.x * grid.y, h->nsm * 8, g.nz, 2);
+  const int kc = (g.nz + zs - 1) / zs;
+  grid.z = (g.nz + kc - 1) / kc;
+  *kchunk = kc;
+  return grid;
+}
+
+// One z-marching pass of a point operation over level geometry g: stencil
+// operations go to the two-points-per-thread driver unless the scalar one was
+// asked for; the rest (restriction, prolongation) use the scalar driver.
 template <bool RED, class Op>
 int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 0) {
   int kc;
+  if constexpr (Zv<Op>::ok) {
+    if (h->zvec) {
+      dim3 grid = zv_grid(h, g, &kc);
+      const int e = cls >= 0 ? tm_begin(h, cls, level) : -1;
+      launch(h, k_zvec<Op, RED>, grid, dim3(ZV_THREADS), 0, op, g, kc, h->partials, h->pstride);
+      ++h->launches;
+      tm_end(h, e, cls, level, (double)g.npts());
+      return grid.x * grid.y * grid.z;
+    }
+  }
   dim3 grid = zm_grid(h, g, &kc);
   const int e = cls >= 0 ? tm_begin(h, cls, level) : -1;
   launch(h, k_zmarch<Op, RED>, grid, dim3(ZM_THREADS), 0, op, g, kc, h->partials, h->pstride);
@@ -292,8 +316,22 @@ int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 
   return grid.x * grid.y * grid.z;
 }
 
+// Pointwise pass over n elements of the finest level: one wave of the kernel's
+// own resident blocks (a grid-stride loop over more blocks than fit at once
+// would leave a partial second wave).
 template <bool RED, class Op> int linear(mg_handle* h, i64 n, const Op& op, int cls = -1) {
-  const int nb = h->lin_grid;
+  static int per_sm = 0;  // per instantiation: resident blocks per SM
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_linear<Op, RED>, LIN_THREADS, 0) != cudaSuccess || v < 1)
+      v = 4;
+    per_sm = v;
+  }
+  const i64 want = (n / 4 + LIN_THREADS - 1) / LIN_THREADS;
+  const i64 wave = (i64)h->nsm * per_sm;
+  int nb = (int)(want < wave ? want : wave);
+  if (nb < 1) nb = 1;
+  if (nb > h->lin_grid) nb = h->lin_grid;
   const int e = cls >= 0 ? tm_begin(h, cls, 0) : -1;
   launch(h, k_linear<Op, RED>, dim3(nb), dim3(LIN_THREADS), 0, op, n, h->partials, h->pstride);
   ++h->launches;
@@ -318,10 +356,31 @@ int level_result_cur(const mg_params& p) {
 }
 
 void cheb_consts(const mg_params& p, double* theta, double* delta, double* sigma) {
+  if (p.smoother == MG_SMOOTHER_RICHARDSON) {  // one step x += omega D^-1 (b - A x) per sweep
+    *theta = 1.0 / p.richardson_omega;
+    *delta = *sigma = 0.0;
+    return;
+  }
   const double beta = p.eig_hi, alpha = p.eig_lo_frac * p.eig_hi;
   *theta = 0.5 * (beta + alpha);
   *delta = 0.5 * (beta - alpha);
   *sigma = *theta / *delta;
+}
+
+// Coefficients of the Chebyshev steps j = 1..degree-1 (the same for every
+// sweep: the recurrence always restarts from rho_0 = 1/sigma), and 1/theta.
+void cheb_table(const mg_params& p, double* inv_theta, double* c1, double* c2) {
+  double theta, delta, sigma;
+  cheb_consts(p, &theta, &delta, &sigma);
+  *inv_theta = 1.0 / theta;
+  double rho_prev = 1.0 / sigma;
+  c1[0] = c2[0] = 0.0;
+  for (int j = 1; j < p.cheby_degree; ++j) {
+    const double rho = 1.0 / (2.0 * sigma - rho_prev);
+    c1[j] = rho * rho_prev;
+    c2[j] = 2.0 * rho / delta;
+    rho_prev = rho;
+  }
 }
 
 template <class TV, class TC> struct Impl {
@@ -555,25 +614,6 @@ template <class TV, class TC> struct Impl {
     return cur;
   }
 
-  // Shared-memory plan of the bottom kernel starting at level l0: arrays are
-  // placed greedily from the coarsest level up while they fit the budget.
-  static int bottom_smem_plan(const mg_handle* h, int l0, int soff[BOT_MAX][BA_N]) {
-    int used = 0;
-    for (int l = 0; l < BOT_MAX; ++l)
-      for (int q = 0; q < BA_N; ++q) soff[l][q] = -1;
-    for (int l = h->L - 1; l >= l0; --l) {
-      const i64 len = h->lv[l].g.len;
-      for (int q = 0; q < BA_N; ++q) {
-        const i64 nb = len * (i64)(q >= BA_KX ? sizeof(TC) : sizeof(TV));
-        if (used + nb <= h->bot_smem_budget) {
-          soff[l - l0][q] = used;
-          used += (int)((nb + 15) / 16 * 16);
-        }
-      }
-    }
-    return used;
-  }
-
   static void bottom(mg_handle* h, int l0) {
     BotArgs<TV, TC> a{};
     a.nlev = h->L - l0;
@@ -594,13 +634,12 @@ template <class TV, class TC> struct Impl {
     a.nu_pre = h->prm.nu_pre;
     a.nu_post = h->prm.nu_post;
     a.degree = h->prm.cheby_degree;
-    cheb_consts(h->prm, &a.theta, &a.delta, &a.sigma);
+    cheb_table(h->prm, &a.inv_theta, a.c1, a.c2);
     a.Lc = h->Lc;
+    a.Li = h->Li;
     a.nc = h->nc;
-    a.result_cur = l0 == h->L - 1 ? 0 : level_result_cur(h->prm);
-    const int smem = bottom_smem_plan(h, l0, a.soff);
     const int e = tm_begin(h, MG_K_BOTTOM, l0);
-    launch(h, k_bottom<TV, TV, TC>, dim3(1), dim3(BOT_THREADS), (size_t)smem, a);
+    launch(h, k_bottom<TV, TV, TC>, dim3(1), dim3(BOT_THREADS), 0, a);
     ++h->launches;
     tm_end(h, e, MG_K_BOTTOM, l0, (double)h->lv[l0].g.npts());
   }
@@ -754,19 +793,6 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   h->lb = L - 1;
   while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
 
-  {
-    int optin = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    h->bot_smem_budget = optin > 24 * 1024 ? optin - 24 * 1024 : 0;  // room for the static arrays
-    dispatch(h, [&](auto impl) {
-      using I = decltype(impl);
-      cudaFuncSetAttribute(k_bottom<typename I::TVt, typename I::TVt, typename I::TCt>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, h->bot_smem_budget);
-      return 0;
-    });
-    cudaGetLastError();
-  }
   const bool mixed = p.precision != MG_FP64;
   const size_t vb = vbytes(h), cb = cbytes(h);
   // cells
@@ -888,19 +914,14 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   // reduction scratch: enough for every reducing launch on the finest level
   int kcz;
   dim3 gz = zm_grid(h, h->lv[0].g, &kcz);
-  {
-    // one full wave of the pointwise kernels: SMs x resident blocks of the
-    // heaviest one (the CG update)
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_linear<LinCgUpd<float, true, true>, true>, LIN_THREADS, 0);
-    if (per_sm < 1) per_sm = 4;
-    const i64 want = (h->lv[0].g.len / 4 + LIN_THREADS - 1) / LIN_THREADS;
-    const i64 wave = (i64)h->nsm * per_sm;
-    h->lin_grid = (int)(want < wave ? want : wave);
-    if (h->lin_grid < 1) h->lin_grid = 1;
-  }
+  // upper bound of the pointwise kernels' grids: every SM full of 256-thread blocks
+  h->lin_grid = h->nsm * (2048 / LIN_THREADS);
   h->pstride = gz.x * gz.y * gz.z;
+  {
+    dim3 gv = zv_grid(h, h->lv[0].g, &kcz);
+    const int vg = gv.x * gv.y * gv.z;
+    if (h->pstride < vg) h->pstride = vg;
+  }
   if (h->pstride < h->lin_grid) h->pstride = h->lin_grid;
   if (h->lv[0].tma) {
     const int tg = h->lv[0].tma_grid[0] * h->lv[0].tma_grid[1] * h->lv[0].tma_grid[2];
@@ -924,6 +945,11 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   CK(cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
   if (bad) return fail(h, MG_ERR_NOT_SPD, "coarsest operator is not positive definite");
+  if (h->nc <= 32) {
+    AL(h->Li, double, 2 * (i64)h->nc * h->nc);
+    k_trinv<<<1, 32, 0, h->s>>>(h->Lc, h->Li, h->nc);
+    CKL();
+  }
   return MG_OK;
 }
 
@@ -1117,6 +1143,8 @@ mg_status mg_params_default(mg_params* p) {
   p->use_graph = 1;
   p->stencil_kernel = 0;
   p->use_pdl = 1;
+  p->smoother = MG_SMOOTHER_CHEBYSHEV;
+  p->richardson_omega = 6.0 / 7.0;
   return MG_OK;
 }
 
@@ -1129,18 +1157,22 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   if (prm) p = *prm;
   else mg_params_default(&p);
   if (Nx < 3 || Ny < 3 || Nz < 3) return fail(nullptr, MG_ERR_ARG, "grid needs at least 3 vertices per axis");
-  if (p.nu_pre < 0 || p.nu_post < 0 || p.cheby_degree < 1 || p.maxit < 0 || !(p.eig_hi > 0) ||
+  if (p.nu_pre < 0 || p.nu_post < 0 || p.cheby_degree < 1 || p.cheby_degree > BOT_MAXDEG || p.maxit < 0 || !(p.eig_hi > 0) ||
       !(p.eig_lo_frac > 0 && p.eig_lo_frac < 1) || p.coarse_k_rule < 0 || p.coarse_k_rule > 2 || p.face_rule < 0 ||
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
-      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 3)
+      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 4 ||
+      p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0))
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible
   // (Polak-Ribiere) beta, which costs one more dot product per iteration.
   if (p.flexible < 0) p.flexible = 0;
+  // Richardson-Jacobi is the degree-1 Chebyshev step with theta = 1 / omega.
+  if (p.smoother == MG_SMOOTHER_RICHARDSON) p.cheby_degree = 1;
   mg_handle* h = new (std::nothrow) mg_handle();
   if (!h) return fail(nullptr, MG_ERR_ALLOC, "host allocation failed");
   h->prm = p;
+  h->zvec = p.stencil_kernel != 4;
   h->us = (cudaStream_t)stream;
   int dev = 0;
   cudaGetDevice(&dev);

@@ -264,6 +264,26 @@ __global__ void k_cholesky(double* A, int n, int* bad) {
     if (t % n > t / n) A[t] = 0.0;
 }
 
+// Inverse of the lower-triangular Cholesky factor L (n <= 32), row-major,
+// for the coarse solve's two triangular products: Li[0, n*n) holds L^-1 and
+// Li[n*n, 2*n*n) its transpose.  Thread c solves L v = e_c by forward
+// substitution (column c of L^-1).
+__global__ void k_trinv(const double* L, double* Li, int n) {
+  const int c = threadIdx.x;
+  if (c >= n) return;
+  double* LiT = Li + (i64)n * n;
+  for (int r = 0; r < n; ++r) {
+    double v = 0.0;
+    if (r >= c) {
+      double s = r == c ? 1.0 : 0.0;
+      for (int q = c; q < r; ++q) s -= L[(i64)r * n + q] * Li[(i64)q * n + c];
+      v = s / L[(i64)r * n + r];
+    }
+    Li[(i64)r * n + c] = v;
+    LiT[(i64)c * n + r] = v;
+  }
+}
+
 // ------------------------------------------------------------ scalars
 enum FinishMode { FIN_BB = 0, FIN_RR = 1, FIN_RZ0 = 2, FIN_PQ = 3, FIN_RZ = 4, FIN_TRUE = 5 };
 
@@ -392,24 +412,22 @@ template <class TV, class TC> struct BotLevel {
   const TC *kx, *ky, *kz;
 };
 
-// Arrays of a bottom level, in the order of BotArgs::soff.
-enum BotArray { BA_X0 = 0, BA_X1, BA_D, BA_B, BA_R, BA_DINV, BA_KX, BA_KY, BA_KZ, BA_N };
+constexpr int BOT_MAXDEG = 32;  // largest Chebyshev degree
 
 template <class TV, class TC> struct BotArgs {
   BotLevel<TV, TC> lv[BOT_MAX];
   int nlev;            // levels in this kernel; the last one is the coarsest
   int nu_pre, nu_post, degree;
-  double theta, delta, sigma;
+  double inv_theta;              // Chebyshev step j = 0: d_0 = s_0 / theta
+  double c1[BOT_MAXDEG], c2[BOT_MAXDEG];  // step j >= 1: d_j = c1[j] d_{j-1} + c2[j] s_j
   const double* Lc;    // Cholesky factor of the coarsest operator (n x n)
+  const double* Li;    // its inverse, then the transpose (n <= 32), else null
   int nc;
-  int soff[BOT_MAX][BA_N];  // byte offset of the array's copy in dynamic shared memory, -1: stays global
-  int result_cur;           // buffer of the first level that holds the result (copied back)
 };
 
 template <class R, class TV, class TC>
 __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const BotArgs<TV, TC>& a) {
-  const R inv_theta = (R)(1.0 / a.theta);
-  double rho_prev = 1.0 / a.sigma;
+  const R inv_theta = (R)a.inv_theta;
   int j0 = 0;
   if (zero) {
     if (a.degree == 1) {
@@ -418,25 +436,16 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
       __syncthreads();
       return cur ^ 1;
     }
-    const double rho = 1.0 / (2.0 * a.sigma - rho_prev);
     OpChebZero<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], a.degree > 2 ? L.d : nullptr, L.kx, L.ky, L.kz,
-                             (R)(rho * rho_prev), (R)(2.0 * rho / a.delta), inv_theta};
+                             (R)a.c1[1], (R)a.c2[1], inv_theta};
     block_for(op, L.g);
     __syncthreads();
     cur ^= 1;
-    rho_prev = rho;
     j0 = 2;
   }
   for (int j = j0; j < a.degree; ++j) {
-    double c1 = 0.0, c2 = 0.0;
-    if (j > 0) {
-      const double rho = 1.0 / (2.0 * a.sigma - rho_prev);
-      c1 = rho * rho_prev;
-      c2 = 2.0 * rho / a.delta;
-      rho_prev = rho;
-    }
     OpChebStep<R, TV, TC> op{L.x[cur], j > 0 ? L.d : nullptr, L.b, L.dinv, L.x[cur ^ 1],
-                             j + 1 < a.degree ? L.d : nullptr, L.kx, L.ky, L.kz, (R)c1, (R)c2, inv_theta};
+                             j + 1 < a.degree ? L.d : nullptr, L.kx, L.ky, L.kz, (R)a.c1[j], (R)a.c2[j], inv_theta};
     block_for(op, L.g);
     __syncthreads();
     cur ^= 1;
@@ -444,41 +453,38 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
   return cur;
 }
 
-// Coarsest solve x = L^-T L^-1 b in float64 by forward and back substitution
-// with the Cholesky factor.  For n <= 32 the factor is staged in shared
-// memory with its reciprocal pivots and one warp substitutes with shuffles
-// (one multiply-add per step); larger n use the whole block.
+// Coarsest solve x = L^-T L^-1 b in float64 with the Cholesky factor.  For
+// n <= 32 the two triangular solves are products with the precomputed L^-1:
+// a substitution is a chain of n dependent divisions and shuffles, slow on
+// GB300's float64 pipe.  Larger n substitute with the whole block.
 template <class TV>
-__device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, int n) {
+__device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, const double* Li, int n) {
   __shared__ double y[1024];
-  __shared__ double Ls[32 * 33];
-  __shared__ double rpiv[32];
+  __shared__ double t[32];
   for (int u = threadIdx.x; u < n; u += blockDim.x) {
     const int i = u % g.nx, j = (u / g.nx) % g.ny, k = u / (g.nx * g.ny);
     y[u] = cvt<double>(b[g.at(i, j, k)]);
   }
-  if (n <= 32) {
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ls[(t / n) * 33 + t % n] = Lc[t];
-    __syncthreads();
+  __syncthreads();
+  if (n <= 32 && Li) {
+    // one warp: lane w forms row w of each product with n multiply-adds (the
+    // float64 pipe issues per warp instruction, so one warp of n steps costs
+    // less than n warps of shuffle-tree sums)
     if (threadIdx.x < 32) {
-      const int l = threadIdx.x;
-      if (l < n) rpiv[l] = 1.0 / Ls[l * 33 + l];
+      const int w = threadIdx.x;
+      double v = 0.0;
+      const double* LiT = Li + n * n;
+      for (int l = 0; l < n; ++l)  // t = L^-1 y (lanes read consecutive entries of the transpose)
+        if (w < n && l <= w) v = fma(LiT[l * n + w], y[l], v);
+      if (w < n) t[w] = v;
       __syncwarp();
-      double v = l < n ? y[l] : 0.0;
-      for (int c = 0; c < n; ++c) {  // forward: L y = b
-        const double yc = __shfl_sync(0xffffffffu, v, c) * rpiv[c];
-        if (l == c) v = yc;
-        if (l > c && l < n) v = fma(-Ls[l * 33 + c], yc, v);
-      }
-      for (int c = n - 1; c >= 0; --c) {  // backward: L^T x = y
-        const double xc = __shfl_sync(0xffffffffu, v, c) * rpiv[c];
-        if (l == c) v = xc;
-        if (l < c) v = fma(-Ls[c * 33 + l], xc, v);
-      }
-      if (l < n) y[l] = v;
+      v = 0.0;
+      for (int l = 0; l < n; ++l)  // y = L^-T t
+        if (w < n && l >= w) v = fma(Li[l * n + w], t[l], v);
+      __syncwarp();
+      if (w < n) y[w] = v;
     }
   } else {
-    __syncthreads();
     for (int c = 0; c < n; ++c) {
       if (threadIdx.x == 0) y[c] /= Lc[(i64)c * n + c];
       __syncthreads();
@@ -500,56 +506,9 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
   __syncthreads();
 }
 
-// out_cur[0] receives the buffer index holding the result on the first level.
-// Copies n bytes (a multiple of 16) between 16-byte aligned buffers.
-__device__ __forceinline__ void block_copy16(void* dst, const void* src, int n) {
-  const int m = n / 16;
-#pragma unroll 4
-  for (int t = threadIdx.x; t < m; t += blockDim.x) ((uint4*)dst)[t] = ((const uint4*)src)[t];
-}
-__device__ __forceinline__ void block_zero16(void* dst, int n) {
-  for (int t = threadIdx.x; t < n / 16; t += blockDim.x) ((uint4*)dst)[t] = make_uint4(0, 0, 0, 0);
-}
-
 template <class R, class TV, class TC>
-__global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> ga) {
+__global__ void __launch_bounds__(BOT_THREADS) k_bottom(const __grid_constant__ BotArgs<TV, TC> a) {
   pdl_wait();
-  // Stage the arrays that fit into shared memory: coefficients, D^-1 and the
-  // right-hand side of the first level are copied in, work vectors start as
-  // zeros (their pads must be zero); the kernel then runs on the staged copies.
-  extern __shared__ __align__(16) unsigned char bsm[];
-  __shared__ BotArgs<TV, TC> a;
-  if (threadIdx.x == 0) a = ga;
-  __syncthreads();
-  for (int l = 0; l < ga.nlev; ++l) {
-    const int bytes_v = (int)(ga.lv[l].g.len * (i64)sizeof(TV)), bytes_c = (int)(ga.lv[l].g.len * (i64)sizeof(TC));
-    const BotLevel<TV, TC>& G = ga.lv[l];
-    const void* src[BA_N] = {G.x[0], G.x[1], G.d, G.b, G.r, G.dinv, G.kx, G.ky, G.kz};
-    for (int q = 0; q < BA_N; ++q) {
-      const int off = ga.soff[l][q];
-      if (off < 0) continue;
-      void* dst = bsm + off;
-      const int nb = q >= BA_KX ? bytes_c : bytes_v;
-      const bool copy_in = q >= BA_DINV || (q == BA_B && l == 0);
-      if (copy_in) block_copy16(dst, src[q], nb);
-      else block_zero16(dst, nb);
-      if (threadIdx.x == 0) {
-        BotLevel<TV, TC>& S = a.lv[l];
-        switch (q) {
-          case BA_X0: S.x[0] = (TV*)dst; break;
-          case BA_X1: S.x[1] = (TV*)dst; break;
-          case BA_D: S.d = (TV*)dst; break;
-          case BA_B: S.b = (TV*)dst; break;
-          case BA_R: S.r = (TV*)dst; break;
-          case BA_DINV: S.dinv = (const TV*)dst; break;
-          case BA_KX: S.kx = (const TC*)dst; break;
-          case BA_KY: S.ky = (const TC*)dst; break;
-          case BA_KZ: S.kz = (const TC*)dst; break;
-        }
-      }
-    }
-  }
-  __syncthreads();
   int cur[BOT_MAX];
   const int L = a.nlev;
   for (int l = 0; l < L - 1; ++l) {
@@ -560,9 +519,6 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> ga) {
       for (i64 t = threadIdx.x; t < V.g.len; t += blockDim.x) V.x[0][t] = store_as<TV>(0.0);
       __syncthreads();
     }
-    double dummy = 0.0, d2 = 0.0;
-    (void)dummy;
-    (void)d2;
     OpResidual<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.kx, V.ky, V.kz};
     block_for(res, V.g);
     __syncthreads();
@@ -570,7 +526,7 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> ga) {
     block_for(rs, a.lv[l + 1].g);
     __syncthreads();
   }
-  bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.nc);
+  bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.Li, a.nc);
   cur[L - 1] = 0;
   for (int l = L - 2; l >= 0; --l) {
     const BotLevel<TV, TC>& V = a.lv[l];
@@ -579,10 +535,6 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(BotArgs<TV, TC> ga) {
     __syncthreads();
     for (int s = 0; s < a.nu_post; ++s) cur[l] = bot_sweep<R>(V, cur[l], false, a);
   }
-  // result of the first level back to its global buffer
-  const int rc = ga.result_cur;
-  if (a.lv[0].x[rc] != ga.lv[0].x[rc])
-    block_copy16(ga.lv[0].x[rc], a.lv[0].x[rc], (int)(ga.lv[0].g.len * (i64)sizeof(TV)));
 }
 
 }  // namespace mgdev

@@ -33,14 +33,17 @@ class Params:
     use_graph: int = 1
     stencil_kernel: int = 0
     use_pdl: int = 1
+    smoother: str = "chebyshev"  # or "richardson" (Jacobi-preconditioned, nu_pre / nu_post iterations)
+    richardson_omega: float = 6.0 / 7.0
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
         L.load().mg_params_default(C.byref(p))
         for name in ("levels", "nu_pre", "nu_post", "cheby_degree", "eig_lo_frac", "eig_hi", "coarse_k_rule",
                      "face_rule", "maxit", "nonzero_guess", "flexible", "telescope_max_n", "use_graph",
-                     "stencil_kernel", "use_pdl"):
+                     "stencil_kernel", "use_pdl", "richardson_omega"):
             setattr(p, name, getattr(self, name))
+        p.smoother = {"chebyshev": 0, "richardson": 1}[self.smoother]
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p

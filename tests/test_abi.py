@@ -50,6 +50,7 @@ def test_params_struct_layout_and_defaults(lib):
     assert (p.nu_pre, p.nu_post, p.cheby_degree) == (1, 1, 2)
     assert (p.eig_lo_frac, p.eig_hi) == (0.1, 2.0)
     assert p.precision == 0 and p.face_rule == 0 and p.coarse_k_rule == 0 and p.flexible == -1
+    assert (p.stencil_kernel, p.use_pdl, p.smoother, p.richardson_omega) == (0, 1, 0, 6.0 / 7.0)
     assert lib.mg_params_default(None) == 1
 
 
@@ -60,8 +61,16 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.mg_setup(None, 9, 9, 9, ctypes.c_void_p(1), 1, None, None) == 1
     p = _lib.MgParams()
     lib.mg_params_default(ctypes.byref(p))
-    p.cheby_degree = 0
+    for bad in (0, 33):  # degrees 1..32
+        p.cheby_degree = bad
+        assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
+        assert b"mg_params" in lib.mg_last_error(None)
+    p.cheby_degree = 2
+    p.stencil_kernel = 5  # kernels 0..4
     assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
-    assert b"mg_params" in lib.mg_last_error(None)
+    p.stencil_kernel = 0
+    for smoother, omega in ((2, 1.0), (1, 0.0), (1, -0.5)):
+        p.smoother, p.richardson_omega = smoother, omega
+        assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
     assert lib.mg_free(None) == 0
     assert lib.mg_num_levels(None) == 0

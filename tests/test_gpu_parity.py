@@ -42,26 +42,37 @@ CASES = [
     ((33, 17, 65), 4, 2.0, dict(face_rule=1, coarse_k_rule=1)),
     ((17, 17, 17), 2, 3.0, dict(cheby_degree=3, nu_pre=2, nu_post=2, coarse_k_rule=2)),
     ((9, 17, 9), 2, 1.0, dict(cheby_degree=1)),
+    ((17, 17, 33), 4, 2.0, dict(cheby_degree=10)),  # Chebyshev(10), Sec. 5
+    ((17, 17, 17), 4, 2.0, dict(smoother="richardson", nu_pre=8, nu_post=8)),  # Richardson(8)-Jacobi, Sec. 5
+    ((17, 9, 17), 2, 1.0, dict(smoother="richardson", richardson_omega=1.0, nu_pre=2, nu_post=3)),
 ]
+
+
+def oracle_for(k, params):
+    """The oracle hierarchy with the same method parameters as a GPU Params dict."""
+    op = params
+    return oracle.Oracle(k, degree=op.get("cheby_degree", 2), nu_pre=op.get("nu_pre", 1), nu_post=op.get("nu_post", 1),
+                         coarse_rule=op.get("coarse_k_rule", 0), face_rule=op.get("face_rule", 0),
+                         smoother=1 if op.get("smoother") == "richardson" else 0,
+                         omega=op.get("richardson_omega", 6.0 / 7.0))
 
 
 def make(dims, block, rng, params, seed=101):
     import paper_1604_07163_gb300 as mg
     k = mi.cell_k(dims, block, -rng, rng, seed)
-    op = {kk: v for kk, v in params.items() if kk in ("face_rule", "coarse_k_rule", "cheby_degree", "nu_pre", "nu_post")}
-    O = oracle.Oracle(k, degree=op.get("cheby_degree", 2), nu_pre=op.get("nu_pre", 1), nu_post=op.get("nu_post", 1),
-                      coarse_rule=op.get("coarse_k_rule", 0), face_rule=op.get("face_rule", 0))
+    O = oracle_for(k, params)
     S = mg.MGSolver(T(k), mg.Params(**params))
     assert S.num_levels == O.levels
     return k, O, S
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_step_parity_fp64(gpu_lib, case, kernel):
-    """kernel 0: default L1 z-marching; 1: plus prolongation folded into the
-    first post-smoothing step on large levels; 2: TMA-staged tiles;
-    3: shared-plane z-marching for every pass."""
+    """kernel 0: default z-marching with two points per thread; 1: plus
+    prolongation folded into the first post-smoothing step on large levels;
+    2: TMA-staged tiles; 3: shared-plane z-marching for every pass;
+    4: z-marching with one point per thread."""
     dims, block, rng, params = CASES[case]
     k, O, S = make(dims, block, rng, dict(params, stencil_kernel=kernel))
     for l in range(O.levels):
@@ -85,7 +96,7 @@ def test_step_parity_fp64(gpu_lib, case, kernel):
     assert relmax(N(S.apply(T(x), -1)), O.apply(x)) < 1e-13
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
 def test_vcycle_parity_large_levels(gpu_lib, kernel):
     """129^3: levels with >= 64 points per axis, where kernel 1 folds the
     coarse-grid correction into the first post-smoothing step; also the
@@ -154,6 +165,23 @@ def test_solve_parity_fp64(gpu_lib, name, n, tol, dit):
     assert np.max(np.abs(h[:m] - info["hist"][:m]) / info["hist"][:m]) < 1e-6
 
 
+@pytest.mark.parametrize("params,dit", [(dict(smoother="richardson", nu_pre=8, nu_post=8), 1),
+                                        (dict(cheby_degree=10), 1)])
+def test_solve_parity_paper_smoothers(gpu_lib, params, dit):
+    """Richardson(8)-Jacobi and Chebyshev(10)-Jacobi, the smoothers of the
+    paper's Sec. 5 runs, on a 65^3 problem with k contrast 10^4: same
+    iteration count as the oracle (within 1) and the same solution."""
+    import paper_1604_07163_gb300 as mg
+    dims = (65, 65, 65)
+    k = mi.cell_k(dims, 8, -2.0, 2.0, 77)
+    f = mi.rhs_f(dims, 77)
+    O = oracle_for(k, params)
+    xo, ito, _ = O.pcg(f, 1e-10, maxit=400)
+    x, st = mg.MGSolver(T(k), mg.Params(maxit=400, **params)).solve(T(f), 1e-10)
+    assert abs(st.iters - ito) <= dit
+    assert rel2(N(x), xo) < 1e-9
+
+
 def test_fixed_iteration_parity_and_not_converged(gpu_lib):
     dims, k, f, spec = mi.workload("poisson33_fp64")
     O = oracle.Oracle(k)
@@ -183,7 +211,7 @@ def test_telescoping_graph_and_kernel_choice_do_not_change_the_result(gpu_lib):
     dims, k, f, spec = mi.workload("poisson33_fp64", 65)
     ref = None
     for tele, graph, kern, pdl in [(0, 0, 1, 0), (4096, 1, 0, 1), (40000, 1, 2, 1), (10 ** 6, 0, 0, 1),
-                                   (4096, 1, 2, 0), (4096, 1, 3, 1)]:
+                                   (4096, 1, 2, 0), (4096, 1, 3, 1), (4096, 1, 4, 1)]:
         x, st = mg.MGSolver(T(k), mg.Params(telescope_max_n=tele, use_graph=graph, stencil_kernel=kern,
                                             use_pdl=pdl)).solve(T(f), 1e-10)
         if ref is None:
@@ -214,7 +242,7 @@ def test_mixed_precision_reaches_fp64_tolerance(gpu_lib, precision):
     assert st.iters <= ito + 6
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("precision,tol", [("mixed_fp32", 2e-6), ("mixed_bf16k", 2e-2)])
 def test_mixed_step_parity(gpu_lib, precision, tol, kernel):
     """float32 vectors: rounding of order 1e-7 relative per step; bfloat16

@@ -238,6 +238,64 @@ def test_chebyshev_error_polynomial_on_eigenvectors(degree):
         assert np.max(np.abs(out0 - (1 - factor) * v)) <= 1e-12
 
 
+@pytest.mark.parametrize("omega", [1.0, 6.0 / 7.0, 0.5])
+def test_richardson_jacobi_error_factor_on_eigenvectors(omega):
+    """Richardson preconditioned with Jacobi, x += omega D^-1 (b - A x): on a
+    constant-k sine mode with D^-1 A eigenvalue mu one iteration multiplies the
+    error by 1 - omega mu; from a zero guess it returns omega D^-1 b."""
+    dims = (17, 17, 17)
+    O = oracle.Oracle(np.ones((16, 16, 16)), levels=1, smoother=1, omega=omega)
+    z, y, x = grid(dims)
+    h = 1.0 / 16
+    D = 6.0 / h ** 2
+    for m in [(1, 1, 1), (5, 2, 7), (15, 15, 15)]:
+        v = np.sin(m[0] * np.pi * z) * np.sin(m[1] * np.pi * y) * np.sin(m[2] * np.pi * x)
+        mu = sum(4.0 / h ** 2 * np.sin(mm * np.pi * h / 2) ** 2 for mm in m) / D
+        out = O.smooth(np.zeros(dims), v)
+        assert np.max(np.abs(out - (1 - omega * mu) * v)) <= 1e-12
+        out0 = O.smooth(O.apply(v))
+        assert np.max(np.abs(out0 - omega * mu * v)) <= 1e-12
+
+
+def test_richardson_vcycle_symmetric_positive_definite_and_mesh_independent():
+    """With the same Richardson iterations before and after the correction the
+    V-cycle is symmetric; with omega D^-1 A of spectral radius below 2 it is
+    positive definite, so CG applies, and (with 8 iterations per level, as in
+    Sec. 5) the CG iteration count does not grow with the mesh."""
+    dims = (17, 17, 17)
+    k = mi.cell_k(dims, 4, -1, 1, seed=9)
+    O = oracle.Oracle(k, nu_pre=8, nu_post=8, smoother=1, omega=6.0 / 7.0)
+    x = mi.random_nodal(dims, 1)
+    y = mi.random_nodal(dims, 2)
+    Mx, My = O.vcycle(x), O.vcycle(y)
+    assert abs(np.sum(Mx * y) - np.sum(x * My)) <= 1e-13 * np.sqrt(np.sum(Mx ** 2) * np.sum(y ** 2))
+    assert np.sum(Mx * x) > 0 and np.sum(My * y) > 0
+    its = []
+    for N in (9, 17, 33, 65):
+        d = (N,) * 3
+        On = oracle.Oracle(np.ones((N - 1,) * 3), nu_pre=8, nu_post=8, smoother=1, omega=6.0 / 7.0)
+        _, it, _ = On.pcg(mi.rhs_f(d, 3), 1e-8)
+        its.append(it)
+    assert max(its) - min(its) <= 2, its
+
+
+def test_chebyshev_degree_10_vcycle_symmetric_and_mesh_independent():
+    """Chebyshev(10)-Jacobi, the smoother of the paper's RASM comparison (Sec. 5)."""
+    its = []
+    for N in (9, 17, 33, 65):
+        d = (N,) * 3
+        On = oracle.Oracle(np.ones((N - 1,) * 3), degree=10)
+        _, it, _ = On.pcg(mi.rhs_f(d, 3), 1e-8)
+        its.append(it)
+    assert max(its) - min(its) <= 2, its
+    dims = (17, 17, 17)
+    O = oracle.Oracle(mi.cell_k(dims, 4, -2, 2, seed=10), degree=10)
+    x = mi.random_nodal(dims, 1)
+    y = mi.random_nodal(dims, 2)
+    Mx, My = O.vcycle(x), O.vcycle(y)
+    assert abs(np.sum(Mx * y) - np.sum(x * My)) <= 1e-13 * np.sqrt(np.sum(Mx ** 2) * np.sum(y ** 2))
+
+
 # ------------------------------------------------------------------ transfers
 def test_prolongation_exact_on_trilinear_functions():
     dims = (17, 17, 17)
