@@ -144,7 +144,7 @@ def whole_job_dofs_per_s(unknowns_per_rank: int, world: int, ms_per_step: float)
     return world * unknowns_per_rank / (ms_per_step * 1e-3)
 
 
-def config_dict(spec, n_ranks, iters=None, name=None, face_rule=0, adjoint=False):
+def config_dict(spec, n_ranks, iters=None, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised"):
     N = spec["N"]
     levels = 1
     M = N
@@ -154,7 +154,8 @@ def config_dict(spec, n_ranks, iters=None, name=None, face_rule=0, adjoint=False
     d = {
         "workload": f"{name or WORKLOAD}: {N}^3 vertices ({(N - 2) ** 3} unknowns), log10 k ~ U[{spec['lo']:g},{spec['hi']:g}] "
                     f"on {spec['block']}^3 cell blocks, f ~ U[-1,1], {'arithmetic' if face_rule else 'harmonic'}-mean "
-                    f"edge k, {levels} levels, V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual "
+                    f"edge k, {levels} levels ({'Galerkin R A P' if coarse_op == 'galerkin' else 're-discretised'} coarse "
+                    f"operators), V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual "
                     f"{spec['rtol']:g}" + ("; step = forward + adjoint solve with the cell gradient" if adjoint else ""),
         "precision": HEADLINE,
         "l2": "no flush: inputs larger than L2 (each float64 vector 134 MB; working set > 2 GB)",
@@ -257,13 +258,15 @@ def run_ours(args):
     phi_obs = None
     if args.adjoint:  # loss 0.5 |phi - phi_obs|^2 with phi_obs from the k field of seed + 1
         kobs = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed + 1), device=dev)
-        So = mg.MGSolver(kobs, mg.Params(precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit))
+        So = mg.MGSolver(kobs, mg.Params(precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit,
+                                         coarse_op=args.coarse_op))
         phi_obs, _ = So.solve(f, rtol, raise_on_error=False)
         So.close()
         del So
 
     for form in run_forms:
-        S = mg.MGSolver(k, mg.Params(precision=form, maxit=args.maxit, face_rule=args.face_rule))
+        S = mg.MGSolver(k, mg.Params(precision=form, maxit=args.maxit, face_rule=args.face_rule,
+                                     coarse_op=args.coarse_op))
         headline = form == HEADLINE
         profile_all = None
         for w in range(args.warmup):
@@ -337,7 +340,8 @@ def run_ours(args):
         speedup = forms["fp64"]["ms_per_step"] / forms[HEADLINE]["ms_per_step"]
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.adjoint:
+    if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.adjoint
+            and args.coarse_op == "rediscretised"):
         its = forms.get("fp64", forms[HEADLINE])["iters"]
         sample = 20
         v, dt, cores = oracle_sample(spec, its, sample)
@@ -351,7 +355,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms[HEADLINE]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic", "config": config_dict(spec, world, forms[HEADLINE]["iters"], args.workload,
-                                                   args.face_rule, args.adjoint),
+                                                   args.face_rule, args.adjoint, args.coarse_op),
         "forms": forms, "speedup_mixed_vs_fp64": speedup,
         "roofline": roofline, "smoother_roofline": smoother, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
@@ -433,6 +437,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(mi.WORKLOADS),
                     help="synthetic workload (the headline metric is quoted on " + WORKLOAD + ")")
     ap.add_argument("--face-rule", type=int, default=0, help="edge k: 0 harmonic (default), 1 arithmetic mean")
+    ap.add_argument("--coarse-op", default="rediscretised", choices=["rediscretised", "galerkin"],
+                    help="coarse operators: re-discretised (default) or Galerkin R A P")
     ap.add_argument("--maxit", type=int, default=3000)
     ap.add_argument("--adjoint", action="store_true", help="each step is a forward + adjoint solve with gradient")
     args = ap.parse_args()

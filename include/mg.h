@@ -70,6 +70,13 @@ typedef enum {
                                  (Sec. 2.1.1; Sec. 5 runs eight iterations per level) */
 } mg_smoother;
 
+typedef enum {
+  MG_COARSE_REDISCRETISED = 0, /* coarse operators re-discretised from averaged cell k (Sec. 1, Sec. 4.3) */
+  MG_COARSE_GALERKIN = 1       /* Galerkin A_{l+1} = R A_l P, 27-point stencils (Sec. 4.3, Sec. 5); each
+                                  Galerkin level's Chebyshev interval is [eig_lo_frac G, G] with G the
+                                  Gershgorin bound of its D^-1 A */
+} mg_coarse_op;
+
 typedef struct {
   int levels;          /* number of levels; 0 = coarsen until an axis has 3 interior points */
   int nu_pre, nu_post; /* smoother sweeps before / after the coarse correction (default 1, 1) */
@@ -102,6 +109,7 @@ typedef struct {
   double richardson_omega; /* Richardson damping, > 0.  The paper gives none; the default 6/7 is
                               the weight that minimises Jacobi's smoothing factor for the 7-point
                               operator (1.0 leaves the highest modes undamped) */
+  int coarse_op;       /* mg_coarse_op (default MG_COARSE_REDISCRETISED) */
 } mg_params;
 
 typedef struct {

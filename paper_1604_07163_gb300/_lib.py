@@ -32,7 +32,7 @@ class MgParams(C.Structure):
         ("coarse_k_rule", C.c_int), ("face_rule", C.c_int), ("k_is_log", C.c_int), ("precision", C.c_int),
         ("maxit", C.c_int), ("nonzero_guess", C.c_int), ("flexible", C.c_int), ("telescope_max_n", C.c_int),
         ("use_graph", C.c_int), ("stencil_kernel", C.c_int), ("use_pdl", C.c_int),
-        ("smoother", C.c_int), ("richardson_omega", C.c_double),
+        ("smoother", C.c_int), ("richardson_omega", C.c_double), ("coarse_op", C.c_int),
     ]
 
 

@@ -18,6 +18,7 @@
 #include "mg_tma.cuh"
 #include "mg_zs.cuh"
 #include "mg_zvec.cuh"
+#include "mg_g27.cuh"
 
 using namespace mgdev;
 
@@ -40,6 +41,14 @@ struct LevelBuf {
   bool tma = false;
   CUtensorMap m_full_x[2], m_full_b, m_full_dinv, m_kx, m_ky, m_kz, m_c_dinv, m_c_b, m_c_d, m_c_r64;
   int tma_grid[3] = {0, 0, 0}, tma_kchunk = 0;
+  // Galerkin (27-point) level: couplings w (13 arrays, V-cycle precision) and
+  // their float64 copies, diagonal in the V-cycle precision and in float64
+  bool g27 = false;
+  void* w = nullptr;
+  double* w64 = nullptr;
+  void* dg = nullptr;
+  double* dg64 = nullptr;
+  double beta = 2.0;  // upper end of the level's Chebyshev interval for D^-1 A
 };
 
 std::string g_setup_error;
@@ -355,13 +364,13 @@ int level_result_cur(const mg_params& p) {
   return f & 1;
 }
 
-void cheb_consts(const mg_params& p, double* theta, double* delta, double* sigma) {
+void cheb_consts(const mg_params& p, double beta_l, double* theta, double* delta, double* sigma) {
   if (p.smoother == MG_SMOOTHER_RICHARDSON) {  // one step x += omega D^-1 (b - A x) per sweep
     *theta = 1.0 / p.richardson_omega;
     *delta = *sigma = 0.0;
     return;
   }
-  const double beta = p.eig_hi, alpha = p.eig_lo_frac * p.eig_hi;
+  const double beta = beta_l, alpha = p.eig_lo_frac * beta_l;
   *theta = 0.5 * (beta + alpha);
   *delta = 0.5 * (beta - alpha);
   *sigma = *theta / *delta;
@@ -369,9 +378,9 @@ void cheb_consts(const mg_params& p, double* theta, double* delta, double* sigma
 
 // Coefficients of the Chebyshev steps j = 1..degree-1 (the same for every
 // sweep: the recurrence always restarts from rho_0 = 1/sigma), and 1/theta.
-void cheb_table(const mg_params& p, double* inv_theta, double* c1, double* c2) {
+void cheb_table(const mg_params& p, double beta_l, double* inv_theta, double* c1, double* c2) {
   double theta, delta, sigma;
-  cheb_consts(p, &theta, &delta, &sigma);
+  cheb_consts(p, beta_l, &theta, &delta, &sigma);
   *inv_theta = 1.0 / theta;
   double rho_prev = 1.0 / sigma;
   c1[0] = c2[0] = 0.0;
@@ -511,7 +520,7 @@ template <class TV, class TC> struct Impl {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
     double theta, delta, sigma;
-    cheb_consts(p, &theta, &delta, &sigma);
+    cheb_consts(p, Lv.beta, &theta, &delta, &sigma);
     const TV inv_theta = (TV)(1.0 / theta);
     for (int j = j_from; j < p.cheby_degree; ++j) {
       double c1 = 0.0, c2 = 0.0;
@@ -541,6 +550,10 @@ template <class TV, class TC> struct Impl {
         else if (j > 0) tma_launch<TK_STEP, true, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
         else if (dot) nb = tma_launch<TK_STEP, false, true>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
         else tma_launch<TK_STEP, false, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
+      } else if (Lv.g27) {  // Galerkin levels are never the finest, so no fused dot
+        OpChebStep27<TV, TV, TC> op{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.w), Lv.g.len,
+                                    (TV)c1, (TV)c2, inv_theta};
+        zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
       } else {
         OpChebStep<TV, TV, TC> op{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
                                   (TV)c1, (TV)c2, inv_theta};
@@ -562,7 +575,7 @@ template <class TV, class TC> struct Impl {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
     double theta, delta, sigma;
-    cheb_consts(p, &theta, &delta, &sigma);
+    cheb_consts(p, Lv.beta, &theta, &delta, &sigma);
     const TV inv_theta = (TV)(1.0 / theta);
     if (!zero) return cheb_steps(h, l, cur, 0, 1.0 / sigma, fuse_rz);
     if (p.cheby_degree == 1) {
@@ -581,6 +594,10 @@ template <class TV, class TC> struct Impl {
     } else if (Lv.tma) {
       tma_launch<TK_ZERO, false, false>(h, l, Lv.m_full_b, &Lv.m_full_dinv, V(Lv.x[cur ^ 1]), dout, c1, c2,
                                         1.0 / theta, MG_K_CHEB_ZERO);
+    } else if (Lv.g27) {
+      OpChebZero27<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), dout, C(Lv.w), Lv.g.len,
+                                  (TV)c1, (TV)c2, inv_theta};
+      zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
     } else {
       OpChebZero<TV, TV, TC> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
                                 (TV)c1, (TV)c2, inv_theta};
@@ -599,7 +616,7 @@ template <class TV, class TC> struct Impl {
     const bool single_step_dot = fuse_rz && p.nu_post == 1 && p.cheby_degree == 1;
     if ((Lv.zs || Lv.zs_prolong) && p.nu_post >= 1 && !single_step_dot) {
       double theta, delta, sigma;
-      cheb_consts(p, &theta, &delta, &sigma);
+      cheb_consts(p, Lv.beta, &theta, &delta, &sigma);
       zs_launch(h, l, PolProlongStep0<TV, TV, TC>{Cv.g, V(Lv.x[cur]), V(Cv.x[ccur]), V(Lv.b), V(Lv.dinv),
                                                   V(Lv.x[cur ^ 1]), p.cheby_degree > 1 ? V(Lv.d) : nullptr,
                                                   C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(1.0 / theta)},
@@ -630,11 +647,13 @@ template <class TV, class TC> struct Impl {
       B.kx = C(Lv.kx);
       B.ky = C(Lv.ky);
       B.kz = C(Lv.kz);
+      B.w = Lv.g27 ? C(Lv.w) : nullptr;
+      B.dg = Lv.g27 ? V(Lv.dg) : nullptr;
+      cheb_table(h->prm, Lv.beta, &B.inv_theta, B.c1, B.c2);
     }
     a.nu_pre = h->prm.nu_pre;
     a.nu_post = h->prm.nu_post;
     a.degree = h->prm.cheby_degree;
-    cheb_table(h->prm, &a.inv_theta, a.c1, a.c2);
     a.Lc = h->Lc;
     a.Li = h->Li;
     a.nc = h->nc;
@@ -653,6 +672,9 @@ template <class TV, class TC> struct Impl {
     } else if (Lv.tma) {
       tma_launch<TK_RESID, false, false>(h, l, Lv.m_full_x[cur], nullptr, V(Lv.r), nullptr, 0.0, 0.0, 0.0,
                                          MG_K_RESID);
+    } else if (Lv.g27) {
+      OpResidual27<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.w), Lv.g.len, V(Lv.dg)};
+      zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
     } else {
       OpResidual<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)};
       zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
@@ -752,6 +774,65 @@ mg_status unpack_level(mg_handle* h, int l, const void* src, double* dst, bool f
   return MG_OK;
 }
 
+// Galerkin level l: A_l = R A_{l-1} P in float64 from the level above (its
+// 7-point edge coefficients or its 27-point couplings), then the V-cycle
+// precision copies, D^-1 and the Gershgorin bound of D^-1 A_l.
+mg_status build_galerkin_level(mg_handle* h, int l) {
+  LevelBuf& Lv = h->lv[l];
+  const LevelBuf& F = h->lv[l - 1];
+  const i64 n = Lv.g.len;
+  const size_t vb = vbytes(h), cb = cbytes(h);
+  Lv.g27 = true;
+  AL(Lv.w64, double, 13 * n);
+  AL(Lv.dg64, double, n);
+  FineOp fo{};
+  fo.g = F.g;
+  if (F.g27) {
+    fo.w = F.w64;
+    fo.dg = F.dg64;
+    fo.wst = F.g.len;
+  } else {
+    fo.kx = F.kx64;
+    fo.ky = F.ky64;
+    fo.kz = F.kz64;
+  }
+  k_galerkin<<<lin_blocks(h, Lv.g.npts()), 128, 0, h->s>>>(fo, Lv.g, Lv.w64, Lv.dg64);
+  CKL();
+  void* q;
+  AL(q, char, 13 * n * (i64)cb);
+  Lv.w = q;
+  AL(q, char, n * (i64)vb);
+  Lv.dg = q;
+  AL(q, char, n * (i64)vb);
+  Lv.dinv = q;
+  const int nb = lin_blocks(h, 13 * n);
+  switch (h->prm.precision) {
+    case MG_MIXED_FP32:
+      k_cast<float, double><<<nb, 256, 0, h->s>>>(Lv.w64, (float*)Lv.w, 13 * n);
+      k_diag27<float><<<lin_blocks(h, Lv.g.npts()), 256, 0, h->s>>>(Lv.dg64, (float*)Lv.dg, (float*)Lv.dinv, Lv.g);
+      break;
+    case MG_MIXED_BF16K:
+      k_cast<__nv_bfloat16, double><<<nb, 256, 0, h->s>>>(Lv.w64, (__nv_bfloat16*)Lv.w, 13 * n);
+      k_diag27<float><<<lin_blocks(h, Lv.g.npts()), 256, 0, h->s>>>(Lv.dg64, (float*)Lv.dg, (float*)Lv.dinv, Lv.g);
+      break;
+    default:
+      k_cast<double, double><<<nb, 256, 0, h->s>>>(Lv.w64, (double*)Lv.w, 13 * n);
+      k_diag27<double><<<lin_blocks(h, Lv.g.npts()), 256, 0, h->s>>>(Lv.dg64, (double*)Lv.dg, (double*)Lv.dinv,
+                                                                       Lv.g);
+  }
+  CKL();
+  CK(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned long long), h->s));
+  k_gershgorin27<<<lin_blocks(h, Lv.g.npts()), 256, 0, h->s>>>(Lv.w64, Lv.dg64, Lv.g,
+                                                               (unsigned long long*)h->dflag);
+  CKL();
+  double gb = 0.0;
+  CK(cudaMemcpyAsync(&gb, h->dflag, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (!(gb > 0.0) || !std::isfinite(gb)) return fail(h, MG_ERR_NOT_SPD, "Galerkin coarse operator has a non-positive diagonal");
+  Lv.beta = gb;
+  return MG_OK;
+}
+
 mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k, int k_on_device) {
   const mg_params& p = h->prm;
   // level count
@@ -822,56 +903,62 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
     LevelBuf& Lv = h->lv[l];
     const i64 n = Lv.g.len;
     void* q;
-    for (void** c : {&Lv.kx, &Lv.ky, &Lv.kz}) {
-      AL(q, char, n * (i64)cb);
-      *c = q;
+    Lv.beta = p.eig_hi;
+    if (l > 0 && p.coarse_op == MG_COARSE_GALERKIN) {
+      mg_status sg = build_galerkin_level(h, l);
+      if (sg != MG_OK) return sg;
+    } else {
+      for (void** c : {&Lv.kx, &Lv.ky, &Lv.kz}) {
+        AL(q, char, n * (i64)cb);
+        *c = q;
+      }
+      const bool need64 = !mixed || l == 0 || l == L - 1;
+      if (mixed && need64) {
+        AL(Lv.kx64, double, n);
+        AL(Lv.ky64, double, n);
+        AL(Lv.kz64, double, n);
+      } else if (!mixed) {
+        Lv.kx64 = (double*)Lv.kx;
+        Lv.ky64 = (double*)Lv.ky;
+        Lv.kz64 = (double*)Lv.kz;
+      }
+      const i64 nbox = (i64)(Lv.g.nx + 1) * (Lv.g.ny + 1) * (Lv.g.nz + 1);
+      const int nb = lin_blocks(h, nbox);
+      switch (p.precision) {
+        case MG_MIXED_FP32:
+          k_build_coef<float><<<nb, 256, 0, h->s>>>(Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule,
+                                                    (float*)Lv.kx, (float*)Lv.ky, (float*)Lv.kz, Lv.kx64, Lv.ky64,
+                                                    Lv.kz64);
+          break;
+        case MG_MIXED_BF16K:
+          k_build_coef<__nv_bfloat16><<<nb, 256, 0, h->s>>>(
+              Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule, (__nv_bfloat16*)Lv.kx,
+              (__nv_bfloat16*)Lv.ky, (__nv_bfloat16*)Lv.kz, Lv.kx64, Lv.ky64, Lv.kz64);
+          break;
+        default:
+          k_build_coef<double><<<nb, 256, 0, h->s>>>(Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule,
+                                                     (double*)Lv.kx, (double*)Lv.ky, (double*)Lv.kz, nullptr,
+                                                     nullptr, nullptr);
+      }
+      CKL();
+      AL(q, char, n * (i64)vb);
+      Lv.dinv = q;
+      const int nbi = lin_blocks(h, Lv.g.npts());
+      switch (p.precision) {
+        case MG_MIXED_FP32:
+          k_dinv<float, float, float><<<nbi, 256, 0, h->s>>>((float*)Lv.kx, (float*)Lv.ky, (float*)Lv.kz,
+                                                             (float*)Lv.dinv, Lv.g);
+          break;
+        case MG_MIXED_BF16K:
+          k_dinv<float, float, __nv_bfloat16><<<nbi, 256, 0, h->s>>>(
+              (__nv_bfloat16*)Lv.kx, (__nv_bfloat16*)Lv.ky, (__nv_bfloat16*)Lv.kz, (float*)Lv.dinv, Lv.g);
+          break;
+        default:
+          k_dinv<double, double, double><<<nbi, 256, 0, h->s>>>((double*)Lv.kx, (double*)Lv.ky, (double*)Lv.kz,
+                                                                (double*)Lv.dinv, Lv.g);
+      }
+      CKL();
     }
-    const bool need64 = !mixed || l == 0 || l == L - 1;
-    if (mixed && need64) {
-      AL(Lv.kx64, double, n);
-      AL(Lv.ky64, double, n);
-      AL(Lv.kz64, double, n);
-    } else if (!mixed) {
-      Lv.kx64 = (double*)Lv.kx;
-      Lv.ky64 = (double*)Lv.ky;
-      Lv.kz64 = (double*)Lv.kz;
-    }
-    const i64 nbox = (i64)(Lv.g.nx + 1) * (Lv.g.ny + 1) * (Lv.g.nz + 1);
-    const int nb = lin_blocks(h, nbox);
-    switch (p.precision) {
-      case MG_MIXED_FP32:
-        k_build_coef<float><<<nb, 256, 0, h->s>>>(Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule,
-                                                  (float*)Lv.kx, (float*)Lv.ky, (float*)Lv.kz, Lv.kx64, Lv.ky64,
-                                                  Lv.kz64);
-        break;
-      case MG_MIXED_BF16K:
-        k_build_coef<__nv_bfloat16><<<nb, 256, 0, h->s>>>(
-            Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule, (__nv_bfloat16*)Lv.kx,
-            (__nv_bfloat16*)Lv.ky, (__nv_bfloat16*)Lv.kz, Lv.kx64, Lv.ky64, Lv.kz64);
-        break;
-      default:
-        k_build_coef<double><<<nb, 256, 0, h->s>>>(Lv.kc, Lv.g, Lv.ih2[0], Lv.ih2[1], Lv.ih2[2], p.face_rule,
-                                                   (double*)Lv.kx, (double*)Lv.ky, (double*)Lv.kz, nullptr,
-                                                   nullptr, nullptr);
-    }
-    CKL();
-    AL(q, char, n * (i64)vb);
-    Lv.dinv = q;
-    const int nbi = lin_blocks(h, Lv.g.npts());
-    switch (p.precision) {
-      case MG_MIXED_FP32:
-        k_dinv<float, float, float><<<nbi, 256, 0, h->s>>>((float*)Lv.kx, (float*)Lv.ky, (float*)Lv.kz,
-                                                           (float*)Lv.dinv, Lv.g);
-        break;
-      case MG_MIXED_BF16K:
-        k_dinv<float, float, __nv_bfloat16><<<nbi, 256, 0, h->s>>>(
-            (__nv_bfloat16*)Lv.kx, (__nv_bfloat16*)Lv.ky, (__nv_bfloat16*)Lv.kz, (float*)Lv.dinv, Lv.g);
-        break;
-      default:
-        k_dinv<double, double, double><<<nbi, 256, 0, h->s>>>((double*)Lv.kx, (double*)Lv.ky, (double*)Lv.kz,
-                                                              (double*)Lv.dinv, Lv.g);
-    }
-    CKL();
     for (void** v : {&Lv.x[0], &Lv.x[1], &Lv.d, &Lv.r}) {
       AL(q, char, n * (i64)vb);
       *v = q;
@@ -898,6 +985,7 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   if (!mixed) h->lv[0].b = h->cr;  // the V-cycle's finest right-hand side is the CG residual
   // TMA-staged stencil kernels on the levels above the bottom kernel
   for (int l = 0; l < h->lb; ++l) {
+    if (h->lv[l].g27) continue;  // the staged kernels read 7-point edge coefficients
     if (p.stencil_kernel == 1 || p.stencil_kernel == 3) {
       dispatch(h, [&](auto impl) {
         decltype(impl)::zs_prepare(h, l);
@@ -936,7 +1024,8 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   // coarsest operator: dense float64 assembly and Cholesky factorisation
   AL(h->Lc, double, (i64)h->nc * h->nc);
   const LevelBuf& Cv = h->lv[L - 1];
-  k_assemble_dense<<<lin_blocks(h, h->nc), 256, 0, h->s>>>(Cv.kx64, Cv.ky64, Cv.kz64, Cv.g, h->Lc);
+  if (Cv.g27) k_assemble_dense27<<<lin_blocks(h, h->nc), 256, 0, h->s>>>(Cv.w64, Cv.dg64, Cv.g, h->Lc);
+  else k_assemble_dense<<<lin_blocks(h, h->nc), 256, 0, h->s>>>(Cv.kx64, Cv.ky64, Cv.kz64, Cv.g, h->Lc);
   CKL();
   CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s));
   k_cholesky<<<1, 1024, 0, h->s>>>(h->Lc, h->nc, h->dflag);
@@ -1145,6 +1234,7 @@ mg_status mg_params_default(mg_params* p) {
   p->use_pdl = 1;
   p->smoother = MG_SMOOTHER_CHEBYSHEV;
   p->richardson_omega = 6.0 / 7.0;
+  p->coarse_op = MG_COARSE_REDISCRETISED;
   return MG_OK;
 }
 
@@ -1161,7 +1251,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       !(p.eig_lo_frac > 0 && p.eig_lo_frac < 1) || p.coarse_k_rule < 0 || p.coarse_k_rule > 2 || p.face_rule < 0 ||
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
       p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 4 ||
-      p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0))
+      p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0) ||
+      p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible
@@ -1185,7 +1276,7 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
     cudaGetLastError();
     s = fail(h, MG_ERR_CUDA, "stream or event creation failed");
   }
-  if (s == MG_OK && (cudaMalloc(&h->dflag, sizeof(int)) != cudaSuccess ||
+  if (s == MG_OK && (cudaMalloc(&h->dflag, sizeof(unsigned long long)) != cudaSuccess ||
                      cudaMallocHost(&h->hsc, sizeof(Scal)) != cudaSuccess)) {
     cudaGetLastError();
     s = fail(h, MG_ERR_ALLOC, "scalar buffers");
@@ -1284,8 +1375,13 @@ mg_status mg_apply(mg_handle* h, int l, const double* x, double* y) {
     using I = decltype(impl);
     using TV = std::remove_pointer_t<decltype(I::V(nullptr))>;
     using TC = std::remove_const_t<std::remove_pointer_t<decltype(I::C(nullptr))>>;
-    OpApply<TV, TV, TC> op{I::V(Lv.x[0]), I::V(Lv.r), I::C(Lv.kx), I::C(Lv.ky), I::C(Lv.kz)};
-    zmarch<false>(h, Lv.g, op);
+    if (Lv.g27) {
+      OpApply27<TV, TV, TC> op{I::V(Lv.x[0]), I::V(Lv.r), I::C(Lv.w), Lv.g.len, I::V(Lv.dg)};
+      zmarch<false>(h, Lv.g, op);
+    } else {
+      OpApply<TV, TV, TC> op{I::V(Lv.x[0]), I::V(Lv.r), I::C(Lv.kx), I::C(Lv.ky), I::C(Lv.kz)};
+      zmarch<false>(h, Lv.g, op);
+    }
     return 0;
   });
   CKL();

@@ -2,6 +2,7 @@
 // data layout and the per-point operations).
 #pragma once
 #include "mg_device.cuh"
+#include "mg_g27.cuh"
 
 namespace mgdev {
 
@@ -401,6 +402,7 @@ __global__ void k_gradient(const double* __restrict__ kc, const double* __restri
 // __syncthreads() between the per-level passes instead of kernel launches.
 constexpr int BOT_MAX = 8;
 constexpr int BOT_THREADS = 1024;
+constexpr int BOT_MAXDEG = 32;  // largest Chebyshev degree
 
 template <class TV, class TC> struct BotLevel {
   Geom g;
@@ -410,16 +412,16 @@ template <class TV, class TC> struct BotLevel {
   TV* r;
   const TV* dinv;
   const TC *kx, *ky, *kz;
+  const TC* w;    // Galerkin level: 13 coupling arrays of length g.len (else null)
+  const TV* dg;   // and its diagonal
+  double inv_theta;                       // Chebyshev step j = 0: d_0 = s_0 / theta
+  double c1[BOT_MAXDEG], c2[BOT_MAXDEG];  // step j >= 1: d_j = c1[j] d_{j-1} + c2[j] s_j
 };
-
-constexpr int BOT_MAXDEG = 32;  // largest Chebyshev degree
 
 template <class TV, class TC> struct BotArgs {
   BotLevel<TV, TC> lv[BOT_MAX];
   int nlev;            // levels in this kernel; the last one is the coarsest
   int nu_pre, nu_post, degree;
-  double inv_theta;              // Chebyshev step j = 0: d_0 = s_0 / theta
-  double c1[BOT_MAXDEG], c2[BOT_MAXDEG];  // step j >= 1: d_j = c1[j] d_{j-1} + c2[j] s_j
   const double* Lc;    // Cholesky factor of the coarsest operator (n x n)
   const double* Li;    // its inverse, then the transpose (n <= 32), else null
   int nc;
@@ -427,7 +429,7 @@ template <class TV, class TC> struct BotArgs {
 
 template <class R, class TV, class TC>
 __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const BotArgs<TV, TC>& a) {
-  const R inv_theta = (R)a.inv_theta;
+  const R inv_theta = (R)L.inv_theta;
   int j0 = 0;
   if (zero) {
     if (a.degree == 1) {
@@ -436,17 +438,30 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
       __syncthreads();
       return cur ^ 1;
     }
-    OpChebZero<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], a.degree > 2 ? L.d : nullptr, L.kx, L.ky, L.kz,
-                             (R)a.c1[1], (R)a.c2[1], inv_theta};
-    block_for(op, L.g);
+    TV* dout = a.degree > 2 ? L.d : nullptr;
+    if (L.w) {
+      OpChebZero27<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], dout, L.w, L.g.len, (R)L.c1[1], (R)L.c2[1], inv_theta};
+      block_for(op, L.g);
+    } else {
+      OpChebZero<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], dout, L.kx, L.ky, L.kz, (R)L.c1[1], (R)L.c2[1], inv_theta};
+      block_for(op, L.g);
+    }
     __syncthreads();
     cur ^= 1;
     j0 = 2;
   }
   for (int j = j0; j < a.degree; ++j) {
-    OpChebStep<R, TV, TC> op{L.x[cur], j > 0 ? L.d : nullptr, L.b, L.dinv, L.x[cur ^ 1],
-                             j + 1 < a.degree ? L.d : nullptr, L.kx, L.ky, L.kz, (R)a.c1[j], (R)a.c2[j], inv_theta};
-    block_for(op, L.g);
+    const TV* dprev = j > 0 ? L.d : nullptr;
+    TV* dout = j + 1 < a.degree ? L.d : nullptr;
+    if (L.w) {
+      OpChebStep27<R, TV, TC> op{L.x[cur], dprev, L.b, L.dinv, L.x[cur ^ 1], dout, L.w, L.g.len,
+                                 (R)L.c1[j], (R)L.c2[j], inv_theta};
+      block_for(op, L.g);
+    } else {
+      OpChebStep<R, TV, TC> op{L.x[cur], dprev, L.b, L.dinv, L.x[cur ^ 1], dout, L.kx, L.ky, L.kz,
+                               (R)L.c1[j], (R)L.c2[j], inv_theta};
+      block_for(op, L.g);
+    }
     __syncthreads();
     cur ^= 1;
   }
@@ -519,8 +534,13 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(const __grid_constant__ 
       for (i64 t = threadIdx.x; t < V.g.len; t += blockDim.x) V.x[0][t] = store_as<TV>(0.0);
       __syncthreads();
     }
-    OpResidual<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.kx, V.ky, V.kz};
-    block_for(res, V.g);
+    if (V.w) {
+      OpResidual27<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.w, V.g.len, V.dg};
+      block_for(res, V.g);
+    } else {
+      OpResidual<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.kx, V.ky, V.kz};
+      block_for(res, V.g);
+    }
     __syncthreads();
     OpRestrict<R, TV> rs{V.g, V.r, a.lv[l + 1].b};
     block_for(rs, a.lv[l + 1].g);

@@ -35,6 +35,7 @@ class Params:
     use_pdl: int = 1
     smoother: str = "chebyshev"  # or "richardson" (Jacobi-preconditioned, nu_pre / nu_post iterations)
     richardson_omega: float = 6.0 / 7.0
+    coarse_op: str = "rediscretised"  # or "galerkin" (R A P, 27-point coarse stencils)
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -44,6 +45,7 @@ class Params:
                      "stencil_kernel", "use_pdl", "richardson_omega"):
             setattr(p, name, getattr(self, name))
         p.smoother = {"chebyshev": 0, "richardson": 1}[self.smoother]
+        p.coarse_op = {"rediscretised": 0, "galerkin": 1}[self.coarse_op]
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p

@@ -50,7 +50,7 @@ def test_params_struct_layout_and_defaults(lib):
     assert (p.nu_pre, p.nu_post, p.cheby_degree) == (1, 1, 2)
     assert (p.eig_lo_frac, p.eig_hi) == (0.1, 2.0)
     assert p.precision == 0 and p.face_rule == 0 and p.coarse_k_rule == 0 and p.flexible == -1
-    assert (p.stencil_kernel, p.use_pdl, p.smoother, p.richardson_omega) == (0, 1, 0, 6.0 / 7.0)
+    assert (p.stencil_kernel, p.use_pdl, p.smoother, p.richardson_omega, p.coarse_op) == (0, 1, 0, 6.0 / 7.0, 0)
     assert lib.mg_params_default(None) == 1
 
 

@@ -296,6 +296,97 @@ def test_chebyshev_degree_10_vcycle_symmetric_and_mesh_independent():
     assert abs(np.sum(Mx * y) - np.sum(x * My)) <= 1e-13 * np.sqrt(np.sum(Mx ** 2) * np.sum(y ** 2))
 
 
+# ------------------------------------------------------------------ Galerkin
+def prolongation_matrix(dims_f):
+    """Trilinear P (fine interior x coarse interior) written from its
+    definition: per axis a fine interior index 2c+1 is coarse node c (weight
+    1), an index 2c lies halfway between coarse nodes c-1 and c (1/2 each)."""
+    nf = [d - 2 for d in dims_f]           # (z, y, x) interior counts
+    nc = [(n - 1) // 2 for n in nf]
+
+    def axis(n_f, n_c):
+        rows, cols, vals = [], [], []
+        for g in range(n_f):
+            if g % 2 == 1:
+                rows.append(g); cols.append((g - 1) // 2); vals.append(1.0)
+            else:
+                for c in (g // 2 - 1, g // 2):
+                    if 0 <= c < n_c:
+                        rows.append(g); cols.append(c); vals.append(0.5)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(n_f, n_c))
+    Pz, Py, Px = (axis(nf[a], nc[a]) for a in range(3))
+    return sp.kron(sp.kron(Pz, Py), Px).tocsr()
+
+
+def test_galerkin_operator_is_the_triple_product():
+    """Coarse operators R A P with R = P^T/8, against scipy sparse products of
+    an independently built P, on two successive levels (7-point fine operator,
+    then a 27-point one)."""
+    dims = (17, 17, 33)
+    k = mi.cell_k(dims, 4, -2, 2, seed=41)
+    O = oracle.Oracle(k, galerkin=True)
+    A = dense_A(O, 0)
+    d = dims
+    for l in (1, 2):
+        P = prolongation_matrix(d)
+        ref = (P.T @ A @ P / 8.0).tocsr()
+        got = dense_A(O, l)
+        assert got.shape == ref.shape
+        assert abs(got - ref).max() <= 1e-12 * abs(ref).max()
+        assert got.nnz <= 27 * got.shape[0]
+        A = got
+        d = tuple((n - 1) // 2 + 1 for n in d)
+
+
+def test_galerkin_coarse_correction_annihilates_the_restricted_residual():
+    """With A_c = R A P an exact coarse-grid correction leaves a residual whose
+    restriction vanishes: R (b - A (x + P A_c^-1 R (b - A x))) = 0.  (A
+    re-discretised coarse operator does not have this property.)"""
+    dims = (9, 17, 17)
+    k = mi.cell_k(dims, 2, -2, 2, seed=42)
+    b = mi.random_nodal(dims, 1)
+    x = mi.random_nodal(dims, 2)
+    for galerkin, small in ((True, True), (False, False)):
+        O = oracle.Oracle(k, levels=2, galerkin=galerkin)
+        bc = O.residual_restrict(b, x)
+        x2 = O.prolong_add(O.coarse_solve(bc), x)
+        after = np.max(np.abs(O.residual_restrict(b, x2))) / np.max(np.abs(bc))
+        assert (after < 1e-12) == small, (galerkin, after)
+
+
+def test_galerkin_chebyshev_interval_is_the_gershgorin_bound():
+    dims = (33, 33, 33)
+    k = mi.cell_k(dims, 4, -3, 3, seed=43)
+    O = oracle.Oracle(k, galerkin=True)
+    assert O.level_beta(0) == 2.0
+    for l in range(1, O.levels):
+        A = dense_A(O, l)
+        g = np.max(np.asarray(abs(A).sum(axis=1)).ravel() / A.diagonal())
+        assert abs(O.level_beta(l) - g) <= 1e-13 * g
+
+
+def test_galerkin_pcg_matches_scipy_cg_and_beats_rediscretisation_at_high_contrast():
+    dims = (33, 33, 33)
+    k = mi.cell_k(dims, 4, -3, 3, seed=44)
+    f = mi.rhs_f(dims, 44)
+    O = oracle.Oracle(k, galerkin=True)
+    x, it, info = O.pcg(f, 1e-10)
+    A = dense_A(O)
+    n = A.shape[0]
+
+    def Minv(r):
+        full = np.zeros(dims)
+        full[1:-1, 1:-1, 1:-1] = r.reshape(31, 31, 31)
+        return interior(O.vcycle(full)).ravel()
+
+    count = [0]
+    xs, flag = spla.cg(A, interior(f).ravel(), rtol=1e-10, atol=0.0, M=spla.LinearOperator((n, n), matvec=Minv),
+                       maxiter=400, callback=lambda xk: count.__setitem__(0, count[0] + 1))
+    assert flag == 0 and abs(count[0] - it) <= 1
+    _, it_r, _ = oracle.Oracle(k).pcg(f, 1e-10, maxit=2000)
+    assert it < it_r
+
+
 # ------------------------------------------------------------------ transfers
 def test_prolongation_exact_on_trilinear_functions():
     dims = (17, 17, 17)
