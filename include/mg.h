@@ -77,6 +77,12 @@ typedef enum {
                                   Gershgorin bound of its D^-1 A */
 } mg_coarse_op;
 
+typedef enum {
+  MG_KRYLOV_CG = 0,     /* preconditioned CG (Sec. 2.1) */
+  MG_KRYLOV_FGMRES = 1  /* flexible GMRES(gmres_restart), right-preconditioned by the V-cycle; classical
+                           Gram-Schmidt; stops on the rotated residual norm (Sec. 5) */
+} mg_krylov;
+
 typedef struct {
   int levels;          /* number of levels; 0 = coarsen until an axis has 3 interior points */
   int nu_pre, nu_post; /* smoother sweeps before / after the coarse correction (default 1, 1) */
@@ -110,6 +116,9 @@ typedef struct {
                               the weight that minimises Jacobi's smoothing factor for the 7-point
                               operator (1.0 leaves the highest modes undamped) */
   int coarse_op;       /* mg_coarse_op (default MG_COARSE_REDISCRETISED) */
+  int krylov;          /* mg_krylov (default MG_KRYLOV_CG) */
+  int gmres_restart;   /* FGMRES restart length m, 1..256 (default 30); the basis takes (m+1) float64
+                          and m V-cycle-precision vectors of the finest level, allocated on first use */
 } mg_params;
 
 typedef struct {

@@ -72,6 +72,8 @@ def _load():
         lib.orc_pcg.restype = C.c_int
         lib.orc_pcg.argtypes = [vp, _dptr, _dptr, C.c_double, C.c_int, C.c_int, C.c_int, vp, _dptr]
         lib.orc_gradient.argtypes = [vp, _dptr, _dptr, _dptr]
+        lib.orc_fgmres.restype = C.c_int
+        lib.orc_fgmres.argtypes = [vp, _dptr, _dptr, C.c_double, C.c_int, C.c_int, vp, _dptr]
         lib.orc_set_smoother.restype = C.c_int
         lib.orc_set_smoother.argtypes = [vp, C.c_int, C.c_double]
         _lib = lib
@@ -195,6 +197,17 @@ class Oracle:
                                0 if x0 is None else 1, hist.ctypes.data, out)
         if it < 0:
             raise FloatingPointError("oracle CG breakdown (p.Ap <= 0)")
+        return x, it, dict(rel_resid=out[0], true_rel_resid=out[1], bnorm=out[2], hist=hist[:it + 1])
+
+    def fgmres(self, f, rtol: float, maxit: int = 500, restart: int = 30):
+        """Flexible GMRES(restart) with the V-cycle as right preconditioner, from
+        x = 0.  Return (x, iterations, info) as pcg does."""
+        x = self._z(0)
+        hist = np.zeros(maxit + 1)
+        out = np.zeros(3)
+        it = self._lib.orc_fgmres(self._h, self._c(f), x, rtol, maxit, restart, hist.ctypes.data, out)
+        if it < 0:
+            raise FloatingPointError("oracle FGMRES breakdown")
         return x, it, dict(rel_resid=out[0], true_rel_resid=out[1], bnorm=out[2], hist=hist[:it + 1])
 
     def gradient(self, phi, lam):

@@ -627,6 +627,97 @@ void orc_smooth(void *hh, int l, const double *bf, double *xf, int zero_guess) {
   free(x);
 }
 
+/* Flexible GMRES(m) preconditioned on the right by the V-cycle (Saad,
+ * Iterative Methods for Sparse Linear Systems, Alg. 9.6), the outer Krylov
+ * method of the paper's Sec. 5 runs.  The Arnoldi basis is orthogonalised by
+ * classical Gram-Schmidt (all coefficients from the same vector, no second
+ * pass); the least-squares problem is reduced by Givens rotations; the
+ * iteration stops when the rotated residual norm |g_{j+1}| <= rtol ||b||, or
+ * after maxit steps, and restarts from the true residual every m steps.
+ * x starts at zero.  Returns the iterations done (-1: breakdown). */
+int orc_fgmres(void *hh, const double *ff, double *xf, double rtol, int maxit, int m, double *hist, double *out) {
+  ohier *H = (ohier *)hh;
+  olevel *L = &H->lv[0];
+  const long n = L->n;
+  if (m < 1) return -1;
+  double *b = (double *)malloc(sizeof(double) * n), *x = (double *)calloc(n, sizeof(double));
+  double *r = (double *)malloc(sizeof(double) * n), *w = (double *)malloc(sizeof(double) * n);
+  double *V = (double *)malloc(sizeof(double) * n * (m + 1)), *Z = (double *)malloc(sizeof(double) * n * m);
+  double *Hs = (double *)calloc((size_t)(m + 1) * m, sizeof(double));
+  double *cs = (double *)malloc(sizeof(double) * m), *sn = (double *)malloc(sizeof(double) * m);
+  double *g = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
+  to_interior(L, ff, b);
+  const double bnorm = sqrt(dot(n, b, b));
+  int it = 0, status = 0;
+  double rnorm = bnorm;
+  if (hist) hist[0] = bnorm > 0 ? 1.0 : 0.0;
+  while (bnorm > 0.0) {
+    spmv(L, x, w); /* restart from the true residual */
+    for (long i = 0; i < n; ++i) r[i] = b[i] - w[i];
+    const double beta = sqrt(dot(n, r, r));
+    rnorm = beta;
+    if (beta <= rtol * bnorm || it >= maxit) break;
+    for (long i = 0; i < n; ++i) V[i] = r[i] / beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    int jj = 0, done = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+      vcycle(H, 0, vj, zj);
+      spmv(L, zj, w);
+      for (int i = 0; i <= j; ++i) Hs[(size_t)i * m + j] = dot(n, w, V + (size_t)i * n);
+      for (int i = 0; i <= j; ++i) {
+        const double hij = Hs[(size_t)i * m + j];
+        const double *vi = V + (size_t)i * n;
+        for (long q = 0; q < n; ++q) w[q] -= hij * vi[q];
+      }
+      const double hn = sqrt(dot(n, w, w));
+      Hs[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0)
+        for (long q = 0; q < n; ++q) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+      for (int i = 0; i < j; ++i) { /* earlier rotations on column j */
+        const double a = Hs[(size_t)i * m + j], c = Hs[(size_t)(i + 1) * m + j];
+        Hs[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        Hs[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = Hs[(size_t)j * m + j], c = Hs[(size_t)(j + 1) * m + j];
+      const double d = sqrt(a * a + c * c);
+      if (!(d > 0.0)) { status = -1; done = 1; break; }
+      cs[j] = a / d;
+      sn[j] = c / d;
+      Hs[(size_t)j * m + j] = d;
+      Hs[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jj = j + 1;
+      rnorm = fabs(g[j + 1]);
+      if (hist) hist[it] = rnorm / bnorm;
+      if (rnorm <= rtol * bnorm || it >= maxit || hn == 0.0) { done = 1; break; }
+    }
+    for (int i = jj - 1; i >= 0; --i) { /* R y = g, then x += Z y */
+      double s = g[i];
+      for (int k = i + 1; k < jj; ++k) s -= Hs[(size_t)i * m + k] * y[k];
+      y[i] = s / Hs[(size_t)i * m + i];
+    }
+    for (int i = 0; i < jj; ++i) {
+      const double *zi = Z + (size_t)i * n;
+      for (long q = 0; q < n; ++q) x[q] += y[i] * zi[q];
+    }
+    if (done) break;
+  }
+  spmv(L, x, w);
+  for (long i = 0; i < n; ++i) w[i] = b[i] - w[i];
+  if (out) {
+    out[0] = bnorm > 0 ? rnorm / bnorm : 0.0;
+    out[1] = bnorm > 0 ? sqrt(dot(n, w, w)) / bnorm : 0.0;
+    out[2] = bnorm;
+  }
+  to_full(L, x, xf);
+  free(b); free(x); free(r); free(w); free(V); free(Z); free(Hs); free(cs); free(sn); free(g); free(y);
+  return status < 0 ? -1 : it;
+}
+
 /* Smoother choice: 0 Chebyshev-Jacobi (default), 1 Richardson-Jacobi with
  * damping omega (one iteration per sweep). */
 int orc_set_smoother(void *hh, int smoother, double omega) {

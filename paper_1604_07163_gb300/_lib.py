@@ -33,6 +33,7 @@ class MgParams(C.Structure):
         ("maxit", C.c_int), ("nonzero_guess", C.c_int), ("flexible", C.c_int), ("telescope_max_n", C.c_int),
         ("use_graph", C.c_int), ("stencil_kernel", C.c_int), ("use_pdl", C.c_int),
         ("smoother", C.c_int), ("richardson_omega", C.c_double), ("coarse_op", C.c_int),
+        ("krylov", C.c_int), ("gmres_restart", C.c_int),
     ]
 
 

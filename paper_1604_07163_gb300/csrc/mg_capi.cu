@@ -19,6 +19,7 @@
 #include "mg_zs.cuh"
 #include "mg_zvec.cuh"
 #include "mg_g27.cuh"
+#include "mg_krylov.cuh"
 
 using namespace mgdev;
 
@@ -65,6 +66,14 @@ struct mg_handle {
   LevelBuf lv[MG_MAX_LEVELS];
   double* Lc = nullptr;  // Cholesky factor of the coarsest operator
   double* Li = nullptr;  // its inverse and the transpose when the coarsest level has at most 32 unknowns
+  // flexible GMRES: basis V_0..V_m (float64), preconditioned Z_0..Z_{m-1}
+  // (V-cycle precision), one column's dots and the coefficients y, partial sums
+  double* kv = nullptr;
+  void* kz = nullptr;
+  double* kh = nullptr;
+  double* kpart = nullptr;
+  double* khost = nullptr;  // pinned mirror of kh
+  int kgrid = 0;
   int nc = 0;
   double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cq = nullptr, *cp = nullptr;
   double* cw = nullptr;    // float64 scratch (gradient input)
@@ -1053,6 +1062,7 @@ void release(mg_handle* h) {
   if (h->s) cudaStreamDestroy(h->s);
   if (h->dflag) cudaFree(h->dflag);
   if (h->hsc) cudaFreeHost(h->hsc);
+  if (h->khost) cudaFreeHost(h->khost);
   delete h;
 }
 
@@ -1208,6 +1218,198 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
   return result;
 }
 
+// Flexible GMRES(m) preconditioned on the right by the V-cycle (Saad, Alg.
+// 9.6), the outer Krylov method of the paper's Sec. 5 runs.  Classical
+// Gram-Schmidt in float64 with the dot products of one column in one pass
+// over the basis; Givens rotations and the small triangular solve on the
+// host; restarts from the true residual every m steps.  Stops when the
+// rotated residual norm |g_{j+1}| <= rtol ||b||.
+mg_status fgmres_alloc(mg_handle* h) {
+  if (h->kv) return MG_OK;
+  const i64 n = h->lv[0].g.len;
+  const int m = h->prm.gmres_restart;
+  h->kgrid = h->nsm * 4;
+  AL(h->kv, double, (i64)(m + 1) * n);
+  void* q;
+  AL(q, char, (i64)m * n * (i64)vbytes(h));
+  h->kz = q;
+  AL(h->kh, double, 2 * (i64)(m + 2));
+  AL(h->kpart, double, (i64)KR_MAXV * h->kgrid);
+  if (cudaMallocHost(&h->khost, sizeof(double) * 2 * (m + 2)) != cudaSuccess) {
+    cudaGetLastError();
+    h->khost = nullptr;
+    return fail(h, MG_ERR_ALLOC, "pinned host allocation failed");
+  }
+  return MG_OK;
+}
+
+// dst[v] = w . V_v for v < nv (V_v = V0 + v * n), in chunks of KR_MAXV vectors
+void mdot(mg_handle* h, const double* w, const double* V0, int nv, double* dst) {
+  const i64 n = h->lv[0].g.len;
+  for (int c = 0; c < nv; c += KR_MAXV) {
+    const int k = nv - c < KR_MAXV ? nv - c : KR_MAXV;
+    k_mdot<<<h->kgrid, KR_THREADS, 0, h->s>>>(w, V0 + (i64)c * n, n, k, n, h->kpart);
+    k_mdot_finish<<<k, KR_THREADS, 0, h->s>>>(h->kpart, h->kgrid, dst + c);
+    h->launches += 2;
+  }
+}
+
+template <class I> mg_status fgmres_impl(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  using TV = typename I::TVt;
+  auto t0 = clk::now();
+  const Geom& g = h->lv[0].g;
+  const LevelBuf& L0 = h->lv[0];
+  const mg_params& p = h->prm;
+  const i64 n = g.len;
+  const int m = p.gmres_restart;
+  h->hist.clear();
+  const long long launches0 = h->launches;
+  mg_status s;
+  if ((s = fgmres_alloc(h)) != MG_OK) return s;
+  if ((s = pack_level(h, 0, f, h->cb, true)) != MG_OK) return s;
+  if (p.nonzero_guess) {
+    if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
+  } else {
+    CK(cudaMemsetAsync(h->cx, 0, (size_t)n * 8, h->s));
+  }
+  CK(cudaMemsetAsync(h->dsc, 0, sizeof(Scal), h->s));
+  int nb = linear<true>(h, n, LinDot<double>{h->cb, h->cb});
+  finish(h, nb, FIN_BB);
+  if ((s = read_scal(h)) != MG_OK) return s;
+  const double bb = h->hsc->bb;
+  if (!std::isfinite(bb)) return fail(h, MG_ERR_NONFINITE, "non-finite value in f");
+  const double bnorm = std::sqrt(bb), tol = rtol * bnorm;
+  const int lb = lin_blocks(h, n);
+  double* V = h->kv;
+  TV* Z = (TV*)h->kz;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1), y(m);
+  mg_status result = MG_OK;
+  int it = 0;
+  double rnorm = 0.0;
+  bool converged = false;
+  while (bnorm > 0.0) {
+    // restart from the true residual r = b - A x
+    OpResidual<double, double, double, double> res{h->cx, h->cb, h->cr, L0.kx64, L0.ky64, L0.kz64};
+    nb = zmarch<true>(h, g, res);
+    finish(h, nb, FIN_RR);
+    if ((s = read_scal(h)) != MG_OK) return s;
+    const double beta = std::sqrt(h->hsc->rr);
+    if (!std::isfinite(beta)) {
+      result = fail(h, MG_ERR_NONFINITE, "non-finite value in x or during the iteration");
+      break;
+    }
+    rnorm = beta;
+    if (h->hist.empty()) h->hist.push_back(beta / bnorm);
+    if (beta <= tol) {
+      converged = true;
+      break;
+    }
+    if (it >= p.maxit) break;
+    k_scale<<<lb, 256, 0, h->s>>>(V, h->cr, 1.0 / beta, n);
+    ++h->launches;
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jj = 0;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = V + (i64)j * n;
+      TV* Zj = Z + (i64)j * n;
+      // z_j = M^-1 v_j: the V-cycle reads the float64 residual buffer (float64
+      // form) or its float32 copy
+      if (p.precision == MG_FP64) {
+        CK(cudaMemcpyAsync(h->cr, Vj, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->s));
+      } else {
+        launch(h, k_cast<TV, double>, dim3(lb), dim3(256), 0, (const double*)Vj, (TV*)L0.b, n);
+        ++h->launches;
+      }
+      TV* zp = nullptr;
+      if ((s = run_precondition<I>(h, &zp)) != MG_OK) return s;
+      CK(cudaMemcpyAsync(Zj, zp, (size_t)n * sizeof(TV), cudaMemcpyDeviceToDevice, h->s));
+      // w = A z_j, then classical Gram-Schmidt against v_0..v_j
+      zmarch<false>(h, g, OpApplyTo64<TV>{Zj, h->cw, L0.kx64, L0.ky64, L0.kz64});
+      mdot(h, h->cw, V, j + 1, h->kh);
+      k_maxpy<double, true><<<lb, 256, 0, h->s>>>(h->cw, V, n, j + 1, h->kh, n);
+      ++h->launches;
+      mdot(h, h->cw, h->cw, 1, h->kh + j + 1);
+      CK(cudaMemcpyAsync(h->khost, h->kh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      tm_collect(h);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h->khost[i];
+      const double hn = std::sqrt(h->khost[j + 1]);
+      if (!std::isfinite(hn)) {
+        result = fail(h, MG_ERR_NONFINITE, "non-finite value during the iteration");
+        stop = true;
+        break;
+      }
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) {
+        k_scale<<<lb, 256, 0, h->s>>>(V + (i64)(j + 1) * n, h->cw, 1.0 / hn, n);
+        ++h->launches;
+      }
+      for (int i = 0; i < j; ++i) {  // earlier rotations on column j
+        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      const double d = std::sqrt(a * a + c * c);
+      if (!(d > 0.0)) {
+        result = fail(h, MG_ERR_BREAKDOWN, "GMRES breakdown: zero column");
+        stop = true;
+        break;
+      }
+      cs[j] = a / d;
+      sn[j] = c / d;
+      H[(size_t)j * m + j] = d;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++it;
+      jj = j + 1;
+      rnorm = std::fabs(gv[j + 1]);
+      h->hist.push_back(rnorm / bnorm);
+      if (rnorm <= tol || it >= p.maxit || hn == 0.0) {
+        stop = true;
+        break;
+      }
+    }
+    // x += Z y with R y = g
+    for (int i = jj - 1; i >= 0; --i) {
+      double v = gv[i];
+      for (int k = i + 1; k < jj; ++k) v -= H[(size_t)i * m + k] * y[k];
+      y[i] = v / H[(size_t)i * m + i];
+    }
+    if (jj > 0) {
+      for (int i = 0; i < jj; ++i) h->khost[i] = y[i];
+      CK(cudaMemcpyAsync(h->kh, h->khost, sizeof(double) * jj, cudaMemcpyHostToDevice, h->s));
+      k_maxpy<TV, false><<<lb, 256, 0, h->s>>>(h->cx, Z, n, jj, h->kh, n);
+      ++h->launches;
+      CK(cudaStreamSynchronize(h->s));  // the pinned y is reused by the next cycle
+    }
+    if (result != MG_OK) break;
+    if (stop && rnorm <= tol) {
+      converged = true;
+      break;
+    }
+    if (stop && it >= p.maxit) break;
+  }
+  if (result == MG_OK && bnorm > 0.0 && !converged)
+    result = fail(h, MG_ERR_NOT_CONVERGED, "maximum number of iterations reached");
+  if ((s = unpack_level(h, 0, h->cx, x, true)) != MG_OK) return s;
+  OpResidual<double, double, double, double> res{h->cx, h->cb, h->cq, L0.kx64, L0.ky64, L0.kz64};
+  nb = zmarch<true>(h, g, res);
+  finish(h, nb, FIN_TRUE);
+  if ((s = read_scal(h)) != MG_OK) return s;
+  h->st.iters = it;
+  h->st.bnorm = bnorm;
+  h->st.rel_resid = bnorm > 0 ? rnorm / bnorm : 0.0;
+  h->st.true_rel_resid = bnorm > 0 ? std::sqrt(h->hsc->true_rr / bb) : 0.0;
+  h->st.solve_s = secs(t0);
+  h->st.kernel_launches = h->launches - launches0;
+  if (st) *st = h->st;
+  return result;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1235,6 +1437,8 @@ mg_status mg_params_default(mg_params* p) {
   p->smoother = MG_SMOOTHER_CHEBYSHEV;
   p->richardson_omega = 6.0 / 7.0;
   p->coarse_op = MG_COARSE_REDISCRETISED;
+  p->krylov = MG_KRYLOV_CG;
+  p->gmres_restart = 30;
   return MG_OK;
 }
 
@@ -1252,7 +1456,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
       p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 4 ||
       p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0) ||
-      p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN)
+      p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN || p.krylov < MG_KRYLOV_CG ||
+      p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible
@@ -1303,6 +1508,8 @@ mg_status mg_set_stream(mg_handle* h, void* stream) {
 mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
   if (!h || !f || !x || !(rtol >= 0)) return h ? fail(h, MG_ERR_ARG, "null pointer or negative rtol") : MG_ERR_ARG;
   Guard guard(h);
+  if (h->prm.krylov == MG_KRYLOV_FGMRES)
+    return dispatch(h, [&](auto impl) { return fgmres_impl<decltype(impl)>(h, f, x, rtol, st); });
   return dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, f, x, rtol, st); });
 }
 

@@ -1,0 +1,85 @@
+// Vector kernels of the flexible GMRES outer iteration (Saad, Iterative
+// Methods for Sparse Linear Systems, Alg. 9.6; the paper's outer Krylov
+// method in Sec. 5).  All arithmetic is float64; the preconditioned vectors
+// z_j are kept in the V-cycle's precision.  Every reduction is a fixed tree
+// (per-thread sums, block sums in index order, then partials in index order),
+// so results repeat bit for bit.
+#pragma once
+#include "mg_device.cuh"
+
+namespace mgdev {
+
+constexpr int KR_THREADS = 256;
+constexpr int KR_MAXV = 8;  // vectors per multi-dot launch
+
+// partials[v * nblocks + block] = sum over this block's elements of w . V_v,
+// for the nv <= KR_MAXV vectors V_v = V0 + v * vst.
+__global__ void __launch_bounds__(KR_THREADS) k_mdot(const double* __restrict__ w, const double* __restrict__ V0,
+                                                     i64 vst, int nv, i64 n, double* partials) {
+  double acc[KR_MAXV];
+#pragma unroll
+  for (int v = 0; v < KR_MAXV; ++v) acc[v] = 0.0;
+  for (i64 t = blockIdx.x * (i64)KR_THREADS + threadIdx.x; t < n; t += (i64)gridDim.x * KR_THREADS) {
+    const double wt = w[t];
+#pragma unroll
+    for (int v = 0; v < KR_MAXV; ++v)
+      if (v < nv) acc[v] = fma(wt, V0[v * vst + t], acc[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < KR_MAXV; v += 2) {
+    double a = acc[v], b = acc[v + 1];
+    block_sum2<KR_THREADS>(a, b);
+    if (threadIdx.x == 0) {
+      if (v < nv) partials[(i64)v * gridDim.x + blockIdx.x] = a;
+      if (v + 1 < nv) partials[(i64)(v + 1) * gridDim.x + blockIdx.x] = b;
+    }
+  }
+}
+
+// out[v] = sum of partials[v * nblocks + 0 .. nblocks-1]; one block per vector
+__global__ void __launch_bounds__(KR_THREADS) k_mdot_finish(const double* partials, int nblocks, double* out) {
+  double a = 0.0, b = 0.0;
+  const double* p = partials + (i64)blockIdx.x * nblocks;
+  for (int t = threadIdx.x; t < nblocks; t += KR_THREADS) a += p[t];
+  block_sum2<KR_THREADS>(a, b);
+  if (threadIdx.x == 0) out[blockIdx.x] = a;
+}
+
+// y[t] -= sum_v c[v] X_v[t] (NEG: Gram-Schmidt update of w) or
+// y[t] += sum_v c[v] X_v[t] (x += Z c at the end of a cycle), for the nv
+// vectors X_v = X0 + v * xst; float X_v are widened on the integer pipe.
+template <class TX, bool NEG>
+__global__ void k_maxpy(double* __restrict__ y, const TX* __restrict__ X0, i64 xst, int nv, const double* c, i64 n) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    double a = y[t];
+    for (int v = 0; v < nv; ++v) a = fma(NEG ? -c[v] : c[v], to_double(X0[v * xst + t]), a);
+    y[t] = a;
+  }
+}
+
+// dst = s * src: a normalised Arnoldi vector (s = 1 / its norm)
+__global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src, double s, i64 n) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    dst[t] = src[t] * s;
+}
+
+// y = A u in float64 for an operand u stored in the V-cycle precision TZ
+template <class TZ> struct OpApplyTo64 {
+  using Real = double;
+  const TZ* u;
+  double* y;
+  const double *kx, *ky, *kz;
+  __device__ void prepare() {}
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double&, double&) const {
+    double D;
+    Ld lu{u};
+    const double S = stencil<NC, double>(g, p, lu, kx, ky, kz, D);
+    y[p] = D * lu(p) - S;
+  }
+  struct Ld {  // float operands widened on the integer pipe
+    const TZ* a;
+    __device__ __forceinline__ double operator()(int q) const { return to_double(__ldg(a + q)); }
+  };
+};
+
+}  // namespace mgdev

@@ -36,6 +36,8 @@ class Params:
     smoother: str = "chebyshev"  # or "richardson" (Jacobi-preconditioned, nu_pre / nu_post iterations)
     richardson_omega: float = 6.0 / 7.0
     coarse_op: str = "rediscretised"  # or "galerkin" (R A P, 27-point coarse stencils)
+    krylov: str = "cg"  # or "fgmres" (flexible GMRES(gmres_restart), right-preconditioned)
+    gmres_restart: int = 30
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -46,6 +48,8 @@ class Params:
             setattr(p, name, getattr(self, name))
         p.smoother = {"chebyshev": 0, "richardson": 1}[self.smoother]
         p.coarse_op = {"rediscretised": 0, "galerkin": 1}[self.coarse_op]
+        p.krylov = {"cg": 0, "fgmres": 1}[self.krylov]
+        p.gmres_restart = self.gmres_restart
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p

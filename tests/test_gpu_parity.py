@@ -211,6 +211,31 @@ def test_galerkin_solve_parity_high_contrast(gpu_lib, precision):
     assert st.iters < it_r  # far fewer than with re-discretised coarse operators
 
 
+@pytest.mark.parametrize("params", [dict(), dict(gmres_restart=5),
+                                    dict(coarse_op="galerkin", smoother="richardson", nu_pre=8, nu_post=8)])
+def test_fgmres_solve_parity(gpu_lib, params):
+    """Flexible GMRES right-preconditioned by the V-cycle (the paper's outer
+    method in Sec. 5; the last case is its configuration: Galerkin coarse
+    operators, Richardson(8)-Jacobi): float64 iteration count within 1 of the
+    oracle's and the same solution; the float32 V-cycle reaches the tolerance."""
+    import paper_1604_07163_gb300 as mg
+    dims = (65, 65, 65)
+    k = mi.cell_k(dims, 8, -2.0, 2.0, 79)
+    f = mi.rhs_f(dims, 79)
+    O = oracle_for(k, params)
+    xo, ito, _ = O.fgmres(f, 1e-10, maxit=400, restart=params.get("gmres_restart", 30))
+    x, st = mg.MGSolver(T(k), mg.Params(maxit=400, krylov="fgmres", **params)).solve(T(f), 1e-10)
+    assert abs(st.iters - ito) <= 1
+    assert rel2(N(x), xo) < 1e-9
+    assert st.true_rel_resid <= 1.05e-10
+    x32, st32 = mg.MGSolver(T(k), mg.Params(maxit=400, krylov="fgmres", precision="mixed_fp32",
+                                            **params)).solve(T(f), 1e-10)
+    assert st32.true_rel_resid <= 1.05e-10
+    assert st32.iters <= ito + 3
+    h = np.asarray(st.history)
+    assert np.all(np.diff(h[1:]) <= 1e-15 + 1e-12 * h[1:-1])  # non-increasing within each cycle's estimate
+
+
 def test_fixed_iteration_parity_and_not_converged(gpu_lib):
     dims, k, f, spec = mi.workload("poisson33_fp64")
     O = oracle.Oracle(k)

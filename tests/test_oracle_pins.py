@@ -387,6 +387,68 @@ def test_galerkin_pcg_matches_scipy_cg_and_beats_rediscretisation_at_high_contra
     assert it < it_r
 
 
+# ------------------------------------------------------------------ FGMRES
+def test_fgmres_residuals_match_an_independent_gmres():
+    """For the (linear, float64) V-cycle M, flexible GMRES without restart is
+    right-preconditioned GMRES: its j-th residual norm is min ||b - A M y||
+    over y in the Krylov space K_j(A M, b).  Here that minimum comes from an
+    Arnoldi process with modified Gram-Schmidt written with numpy, and a
+    least-squares solve, independent of the oracle's classical Gram-Schmidt
+    and Givens rotations."""
+    dims = (17, 17, 17)
+    k = mi.cell_k(dims, 4, -2, 2, seed=51)
+    f = mi.rhs_f(dims, 51)
+    O = oracle.Oracle(k)
+    x, it, info = O.fgmres(f, 1e-10, restart=40, maxit=12)
+    A = dense_A(O)
+    n = A.shape[0]
+
+    def M(v):
+        full = np.zeros(dims)
+        full[1:-1, 1:-1, 1:-1] = v.reshape(15, 15, 15)
+        return interior(O.vcycle(full)).ravel()
+
+    b = interior(f).ravel()
+    beta = np.linalg.norm(b)
+    Q = [b / beta]
+    Hm = np.zeros((13, 12))
+    for j in range(12):
+        w = A @ M(Q[j])
+        for i in range(j + 1):
+            Hm[i, j] = w @ Q[i]
+            w = w - Hm[i, j] * Q[i]
+        Hm[j + 1, j] = np.linalg.norm(w)
+        Q.append(w / Hm[j + 1, j])
+        e = np.zeros(j + 2)
+        e[0] = beta
+        yv, *_ = np.linalg.lstsq(Hm[:j + 2, :j + 1], e, rcond=None)
+        ref = np.linalg.norm(e - Hm[:j + 2, :j + 1] @ yv) / beta
+        assert abs(info["hist"][j + 1] - ref) <= 1e-8 * ref + 1e-14, (j, info["hist"][j + 1], ref)
+
+
+def test_fgmres_exact_preconditioner_and_agreement_with_cg():
+    """One level: the preconditioner is the exact Cholesky solve, so one
+    FGMRES iteration solves the system; on a multigrid hierarchy FGMRES (with
+    and without restarts) and CG reach the same solution, with non-increasing
+    residual estimates."""
+    dims = (9, 9, 9)
+    k = mi.cell_k(dims, 2, -1, 1, seed=52)
+    f = mi.rhs_f(dims, 52)
+    O1 = oracle.Oracle(k, levels=1)
+    x1, it1, info1 = O1.fgmres(f, 1e-12)
+    assert it1 == 1 and info1["true_rel_resid"] < 1e-13
+    dims = (33, 33, 33)
+    k = mi.cell_k(dims, 4, -1, 1, seed=53)
+    f = mi.rhs_f(dims, 53)
+    O = oracle.Oracle(k)
+    xc, itc, _ = O.pcg(f, 1e-11)
+    for m in (30, 4):
+        x, it, info = O.fgmres(f, 1e-11, restart=m)
+        assert info["true_rel_resid"] <= 1.01e-11
+        assert np.all(np.diff(info["hist"]) <= 1e-15)
+        assert np.linalg.norm(x - xc) <= 1e-9 * np.linalg.norm(xc)
+
+
 # ------------------------------------------------------------------ transfers
 def test_prolongation_exact_on_trilinear_functions():
     dims = (17, 17, 17)
