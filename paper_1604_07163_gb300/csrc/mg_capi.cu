@@ -311,11 +311,32 @@ dim3 zv_grid(const mg_handle* h, const Geom& g, int* kchunk) {
 }
 
 // One z-marching pass of a point operation over level geometry g: stencil
-// operations go to the two-points-per-thread driver unless the scalar one was
-// asked for; the rest (restriction, prolongation) use the scalar driver.
+// operations, the prolongation and the restriction go to the two-points-per-
+// thread kernels unless the scalar driver was asked for (the float64 CG
+// operator and the 27-point operators always use the scalar driver).
+
+template <class R, class TV> void zv_xfer(mg_handle* h, const Geom& gc, const OpRestrict<R, TV>& op) {
+  int kc;
+  dim3 grid = zv_grid(h, gc, &kc);
+  launch(h, k_restrict_v<R, TV>, grid, dim3(ZV_THREADS), 0, op, gc, kc);
+}
+template <class R, class TV> void zv_xfer(mg_handle* h, const Geom& g, const OpProlong<R, TV>& op) {
+  dim3 grid((g.nx + 255) / 256, (g.ny + 3) / 4, g.nz);
+  launch(h, k_prolong_v<R, TV>, grid, dim3(PV_THREADS), 0, op, g);
+}
+
 template <bool RED, class Op>
 int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 0) {
   int kc;
+  if constexpr (ZvXfer<Op>::ok) {  // prolongation / restriction: vector kernels
+    if (h->zvec) {
+      const int e = cls >= 0 ? tm_begin(h, cls, level) : -1;
+      zv_xfer(h, g, op);
+      ++h->launches;
+      tm_end(h, e, cls, level, (double)g.npts());
+      return 0;
+    }
+  }
   if constexpr (Zv<Op>::ok) {
     if (h->zvec) {
       dim3 grid = zv_grid(h, g, &kc);

@@ -413,4 +413,153 @@ __global__ void __launch_bounds__(ZV_THREADS, ZvMinBlocks<Op>::value)
   }
 }
 
+// ------------------------------------------------------------ transfers
+// x += P e on the fine grid (OpProlong) without z-marching: each thread
+// updates four consecutive fine points of one row (one 16-byte access to x in
+// float32, two in float64); the twelve coarse values they draw on (coarse
+// columns 2m-1 .. 2m+1, two rows, two planes) come through L1.  A thread
+// owns one row chunk, so many independent read-modify-writes are in flight.
+// Same terms in the same order as OpProlong.
+constexpr int PV_THREADS = 256;  // 64 chunks of 4 points x 4 rows
+template <class R, class TV>
+__global__ void __launch_bounds__(PV_THREADS) k_prolong_v(OpProlong<R, TV> op, Geom g) {
+  pdl_wait();
+  const int chunk = blockIdx.x * 64 + (threadIdx.x & 63);
+  const int j = blockIdx.y * 4 + (threadIdx.x >> 6);
+  const int k = blockIdx.z;
+  const int i = 4 * chunk;
+  if (j < g.ny && i < g.nx) {
+    const Geom& gc = op.gc;
+    const int m = chunk;  // fine i = 4m: coarse columns 2m-1, 2m, 2m+1
+    const int jr[2] = {(j - 1) >> 1, j >> 1}, kp[2] = {(k - 1) >> 1, k >> 1};
+    R E[2][2][3];  // [plane k0/k1][row j0/j1][column 2m-1 .. 2m+1]
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const i64 q = gc.at(2 * m - 1, jr[r], kp[a]);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) E[a][r][cc] = cvt<R>(__ldg(op.e + q + cc));
+      }
+    const i64 p = g.at(i, j, k);
+    R xv[4];
+    if constexpr (sizeof(TV) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(op.x + p);
+      xv[0] = t.x, xv[1] = t.y, xv[2] = t.z, xv[3] = t.w;
+    } else {
+      const double2 t0 = *reinterpret_cast<const double2*>(op.x + p);
+      const double2 t1 = *reinterpret_cast<const double2*>(op.x + p + 2);
+      xv[0] = t0.x, xv[1] = t0.y, xv[2] = t1.x, xv[3] = t1.y;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      // coarse columns of fine 4m+e: i0 = (4m+e-1)>>1, i1 = (4m+e)>>1, as offsets from 2m-1
+      const int c0 = (e + 1) >> 1, c1 = (e + 2) >> 1;
+      R sum = E[0][0][c0] + E[0][0][c1];
+      sum += E[0][1][c0] + E[0][1][c1];
+      sum += E[1][0][c0] + E[1][0][c1];
+      sum += E[1][1][c0] + E[1][1][c1];
+      xv[e] = fma((R)0.125, sum, xv[e]);
+    }
+    const int nv = min(g.nx - i, 4);
+    if (nv == 4) {
+      if constexpr (sizeof(TV) == 4) {
+        *reinterpret_cast<float4*>(op.x + p) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+      } else {
+        reinterpret_cast<double2*>(op.x + p)[0] = make_double2(xv[0], xv[1]);
+        reinterpret_cast<double2*>(op.x + p)[1] = make_double2(xv[2], xv[3]);
+      }
+    } else {
+      for (int e = 0; e < nv; ++e) op.x[p + e] = store_as<TV>(xv[e]);
+    }
+  }
+  pdl_trigger();
+}
+
+// bc = R r on the coarse grid (OpRestrict), two coarse points (c, c+1) per
+// thread: the five fine values 2c .. 2c+4 of a fine row come from one
+// 16-byte load and the right lane's first value.  Per fine plane the three
+// fine rows give the plane sum; consecutive coarse planes share a fine plane,
+// whose sum is kept.  Same terms in the same order as OpRestrict.
+template <class R, class TV>
+__global__ void __launch_bounds__(ZV_THREADS, 8) k_restrict_v(OpRestrict<R, TV> op, Geom gc, int kchunk) {
+  pdl_wait();
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * ZV_TX + 2 * lane;
+  const int cj = blockIdx.y * ZV_TY + (threadIdx.x >> 5);
+  const int k0 = blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, gc.nz);
+  if (cj < gc.ny) {
+    const Geom& gf = op.gf;
+    const int nv = min(max(gc.nx - c, 0), 2);
+    const int fb = min(2 * c, gf.Px - 4);  // fine x of the first of the five values (a multiple of 4)
+    // plane sum of fine plane kf for the two coarse points
+    auto plane = [&](int kf, R (&P)[2]) {
+      R row[3][2];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int q = (int)gf.at(fb, 2 * cj + b, kf);
+        R v[5];
+        if constexpr (sizeof(TV) == 4) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(op.r + q));
+          v[0] = cvt<R>(t.x), v[1] = cvt<R>(t.y), v[2] = cvt<R>(t.z), v[3] = cvt<R>(t.w);
+        } else {
+          const double2 t0 = __ldg(reinterpret_cast<const double2*>(op.r + q));
+          const double2 t1 = __ldg(reinterpret_cast<const double2*>(op.r + q + 2));
+          v[0] = cvt<R>(t0.x), v[1] = cvt<R>(t0.y), v[2] = cvt<R>(t1.x), v[3] = cvt<R>(t1.y);
+        }
+        v[4] = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (lane == 31) v[4] = cvt<R>(__ldg(op.r + q + 4));
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          row[b][e] = fma((R)0.5, v[2 * e + 1], (R)0.25 * (v[2 * e] + v[2 * e + 2]));
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        R pl = 0;
+        pl = fma((R)0.25, row[0][e], pl);
+        pl = fma((R)0.5, row[1][e], pl);
+        pl = fma((R)0.25, row[2][e], pl);
+        P[e] = pl;
+      }
+    };
+    R Plo[2], Pmid[2], Phi[2];
+    plane(2 * k0, Plo);
+    for (int k = k0; k < k1; ++k) {
+      if (k + 1 < k1) {  // the fine rows of the next coarse plane into L2
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          pf_l2(op.r + gf.at(fb, 2 * cj + b, 2 * k + 3));
+          pf_l2(op.r + gf.at(fb, 2 * cj + b, 2 * k + 4));
+        }
+      }
+      plane(2 * k + 1, Pmid);
+      plane(2 * k + 2, Phi);
+      R acc[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        R a = 0;
+        a = fma((R)0.25, Plo[e], a);
+        a = fma((R)0.5, Pmid[e], a);
+        a = fma((R)0.25, Phi[e], a);
+        acc[e] = a;
+      }
+      if (nv > 0) st2(op.bc + gc.at(min(c, gc.Px - 2), cj, k), acc, nv);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) Plo[e] = Phi[e];
+    }
+  }
+  pdl_trigger();
+}
+
+template <class Op> struct ZvXfer {
+  static constexpr bool ok = false;
+};
+template <class R, class TV> struct ZvXfer<OpProlong<R, TV>> {
+  static constexpr bool ok = true;
+};
+template <class R, class TV> struct ZvXfer<OpRestrict<R, TV>> {
+  static constexpr bool ok = true;
+};
+
 }  // namespace mgdev
