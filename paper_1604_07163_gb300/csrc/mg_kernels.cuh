@@ -521,9 +521,38 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
   __syncthreads();
 }
 
+// L2 prefetch of n bytes at p, one 128-byte line per thread and step
+__device__ __forceinline__ void block_prefetch_l2(const void* p, i64 n) {
+  if (!p) return;
+  for (i64 o = (i64)threadIdx.x * 128; o < n; o += (i64)blockDim.x * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)p + o));
+}
+
 template <class R, class TV, class TC>
 __global__ void __launch_bounds__(BOT_THREADS) k_bottom(const __grid_constant__ BotArgs<TV, TC> a) {
   pdl_wait();
+  // The streaming passes on the fine levels evict these small arrays from L2
+  // between V-cycles: request all of them at once instead of meeting the
+  // misses one pass at a time.
+  for (int l = 0; l < a.nlev; ++l) {
+    const BotLevel<TV, TC>& V = a.lv[l];
+    const i64 nv = V.g.len * (i64)sizeof(TV), nc = V.g.len * (i64)sizeof(TC);
+    block_prefetch_l2(V.x[0], nv);
+    block_prefetch_l2(V.x[1], nv);
+    block_prefetch_l2(V.d, nv);
+    block_prefetch_l2(V.b, nv);
+    block_prefetch_l2(V.r, nv);
+    block_prefetch_l2(V.dinv, nv);
+    if (V.w) {
+      block_prefetch_l2(V.w, 13 * nc);
+      block_prefetch_l2(V.dg, nv);
+    } else {
+      block_prefetch_l2(V.kx, nc);
+      block_prefetch_l2(V.ky, nc);
+      block_prefetch_l2(V.kz, nc);
+    }
+  }
+  if (a.Li) block_prefetch_l2(a.Li, 2 * (i64)a.nc * a.nc * (i64)sizeof(double));
   int cur[BOT_MAX];
   const int L = a.nlev;
   for (int l = 0; l < L - 1; ++l) {
