@@ -407,6 +407,49 @@ def test_adjoint_gradient_parity_129(gpu_lib):
     assert rel2(N(logk.grad), grad_o) < 1e-8
 
 
+@pytest.mark.parametrize("params", [dict(coarse_op="galerkin"),
+                                    dict(coarse_op="galerkin", krylov="fgmres", precision="mixed_fp32")])
+def test_adjoint_gradient_with_galerkin_and_fgmres(gpu_lib, params):
+    """The gradient depends only on the finest operator and the converged
+    forward and adjoint solutions, not on the preconditioner or the outer
+    method: with Galerkin coarse operators (and FGMRES around a float32
+    V-cycle) it matches the oracle's gradient from its own CG solves."""
+    import paper_1604_07163_gb300 as mg
+    dims = (33, 33, 33)
+    k = mi.cell_k(dims, 4, -2.0, 2.0, 81)
+    f = mi.rhs_f(dims, 81)
+    mask = mi.obs_mask(dims, 81)
+    O = oracle.Oracle(k)
+    phi_o, _, _ = O.pcg(f, 1e-13)
+    g_o = np.where(mask, phi_o, 0.0)
+    lam_o, _, _ = O.pcg(g_o, 1e-13)
+    grad_o = O.gradient(phi_o, lam_o)
+    S = mg.MGSolver(T(k), mg.Params(maxit=500, **params))
+    phi, st = S.solve(T(f), 1e-12)
+    lam, grad, st2 = S.solve_adjoint(T(np.where(mask, N(phi), 0.0)), 1e-12, phi)
+    assert rel2(N(phi), phi_o) < 1e-10
+    assert rel2(N(lam), lam_o) < 1e-9
+    assert rel2(N(grad), grad_o) < 1e-8
+
+
+def test_fgmres_nonzero_initial_guess(gpu_lib):
+    """FGMRES from a nonzero initial guess: restarts from b - A x0, reaches
+    the same solution in fewer iterations when x0 is close."""
+    import paper_1604_07163_gb300 as mg
+    dims = (33, 33, 33)
+    k = mi.cell_k(dims, 4, -1.0, 1.0, 82)
+    f = mi.rhs_f(dims, 82)
+    xo, _, _ = oracle.Oracle(k).pcg(f, 1e-13)
+    S0 = mg.MGSolver(T(k), mg.Params(krylov="fgmres"))
+    _, st0 = S0.solve(T(f), 1e-10)
+    S = mg.MGSolver(T(k), mg.Params(krylov="fgmres", nonzero_guess=1))
+    x0 = T(xo * (1.0 + 1e-6 * mi.random_nodal(dims, 5)))
+    x, st = S.solve(T(f), 1e-10, x=x0)
+    assert st.true_rel_resid <= 1.05e-10
+    assert st.iters < st0.iters
+    assert rel2(N(x), xo) < 1e-9
+
+
 def test_gradient_finite_differences_gpu(gpu_lib):
     """Central differences (h = 1e-6, forward solves to 1e-13) on 32 seeded cells."""
     import paper_1604_07163_gb300 as mg
