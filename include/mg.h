@@ -119,6 +119,11 @@ typedef struct {
   int krylov;          /* mg_krylov (default MG_KRYLOV_CG) */
   int gmres_restart;   /* FGMRES restart length m, 1..256 (default 30); the basis takes (m+1) float64
                           and m V-cycle-precision vectors of the finest level, allocated on first use */
+  int eig_mode;        /* Chebyshev interval of every level: 0 (default) [eig_lo_frac b, b] with b = eig_hi
+                          (the Gershgorin bound on Galerkin levels); 1 [eig_lo_frac L, eig_safety L] with L
+                          a 10-step CG-Lanczos estimate of the largest eigenvalue of D^-1 A on the level,
+                          from a seeded random right-hand side (computed at setup) */
+  double eig_safety;   /* upper factor of eig_mode 1 (default 1.1) */
 } mg_params;
 
 typedef struct {
@@ -174,6 +179,8 @@ const char* mg_last_error(const mg_handle* h);
 int mg_num_levels(const mg_handle* h);
 /* Vertex counts of level l (0 = finest) into N3 = {Nx, Ny, Nz}. */
 mg_status mg_level_dims(const mg_handle* h, int l, int* N3);
+/* Chebyshev interval [*alpha, *beta] of D^-1 A used by the smoother on level l. */
+mg_status mg_level_interval(const mg_handle* h, int l, double* alpha, double* beta);
 /* Copy up to cap entries of the last solve's ||r_k||/||b|| history to the
  * host array hist; returns the number available. */
 int mg_history(const mg_handle* h, double* hist, int cap);

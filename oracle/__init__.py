@@ -54,6 +54,12 @@ def _load():
                                        C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]
         lib.orc_level_beta.restype = C.c_double
         lib.orc_level_beta.argtypes = [vp, C.c_int]
+        lib.orc_level_alpha.restype = C.c_double
+        lib.orc_level_alpha.argtypes = [vp, C.c_int]
+        lib.orc_level_lanczos.restype = C.c_double
+        lib.orc_level_lanczos.argtypes = [vp, C.c_int]
+        lib.orc_set_eig_mode.restype = C.c_int
+        lib.orc_set_eig_mode.argtypes = [vp, C.c_int, C.c_double]
         lib.orc_free.argtypes = [vp]
         lib.orc_num_levels.argtypes = [vp]
         lib.orc_level_dims.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
@@ -96,10 +102,12 @@ class Oracle:
     def __init__(self, k_cells, levels: int | None = None, nu_pre: int = 1, nu_post: int = 1,
                  degree: int = 2, eig_lo_frac: float = 0.1, eig_hi: float = 2.0,
                  coarse_rule: int = 0, face_rule: int = 0, smoother: int = 0, omega: float = 6.0 / 7.0,
-                 galerkin: bool = False):
+                 galerkin: bool = False, eig_mode: int = 0, eig_safety: float = 1.1):
         """smoother 0: Chebyshev(degree)-Jacobi sweeps; 1: Richardson-Jacobi
         iterations x += omega D^-1 (b - A x), nu_pre / nu_post of them.
-        galerkin: coarse operators R A P instead of re-discretisation."""
+        galerkin: coarse operators R A P instead of re-discretisation.
+        eig_mode 1: per-level Chebyshev interval [eig_lo_frac L, eig_safety L]
+        from a 10-step Lanczos estimate L of the largest eigenvalue of D^-1 A."""
         lib = _load()
         k = np.ascontiguousarray(k_cells, dtype=np.float64)
         self.dims = tuple(s + 1 for s in k.shape)
@@ -112,6 +120,8 @@ class Oracle:
         self._lib = lib
         if lib.orc_set_smoother(self._h, smoother, omega) != 0:
             raise ValueError("oracle: invalid smoother")
+        if eig_mode and lib.orc_set_eig_mode(self._h, eig_mode, eig_safety) != 0:
+            raise ValueError("oracle: invalid eigenvalue-estimate mode")
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -121,6 +131,14 @@ class Oracle:
     def level_beta(self, l: int) -> float:
         """Upper end of level l's Chebyshev interval."""
         return self._lib.orc_level_beta(self._h, l)
+
+    def level_alpha(self, l: int) -> float:
+        """Lower end of level l's Chebyshev interval."""
+        return self._lib.orc_level_alpha(self._h, l)
+
+    def level_lanczos(self, l: int) -> float:
+        """Lanczos estimate of the largest eigenvalue of D^-1 A on level l."""
+        return self._lib.orc_level_lanczos(self._h, l)
 
     def level_dims(self, l: int):
         N = (C.c_int * 3)()

@@ -69,6 +69,7 @@ typedef struct {
   int coarse_rule;     /* 0 arithmetic, 1 geometric, 2 harmonic mean of children */
   int face_rule;       /* edge k: 0 harmonic, 1 arithmetic mean of the 4 cells */
   int galerkin;        /* coarse operators: 0 re-discretised, 1 Galerkin R A P */
+  int eig_mode;        /* Chebyshev interval: 0 fixed / Gershgorin, 1 Lanczos estimate */
   double *Ac, *Lc;     /* dense coarsest operator and its Cholesky factor */
 } ohier;
 
@@ -332,6 +333,83 @@ static double gershgorin(const olevel *L) {
   return g;
 }
 
+/* ------------------------------------------------------------ eigen-estimate */
+/* Counter-based uniform numbers in [0,1): Vigna's SplitMix64 finaliser,
+ * u(seed, stream, idx) = (sm(sm(seed ^ stream << 56) ^ idx) >> 11) 2^-53. */
+static uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static double uniform01(uint64_t seed, uint64_t stream, uint64_t idx) {
+  return (double)(splitmix64(splitmix64(seed ^ (stream << 56)) ^ idx) >> 11) * (1.0 / 9007199254740992.0);
+}
+#define ORC_EIG_SEED 20160424ull
+#define ORC_EIG_STEPS 10
+
+/* Number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm
+ * sequence of the LDL^T pivots). */
+static int sturm_below(int m, const double *d, const double *e, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; ++i) {
+    q = d[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+/* Largest eigenvalue of D^-1 A on a level, estimated by CG with the Jacobi
+ * preconditioner for ORC_EIG_STEPS steps from a seeded random right-hand side
+ * (entries u - 1/2, stream 3, index = interior point number) and a zero guess.
+ * The CG coefficients give the Lanczos tridiagonal matrix of the
+ * preconditioned operator (Saad, Iterative Methods, Sec. 6.7.3):
+ * T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j;
+ * its largest eigenvalue by bisection. */
+static double lanczos_lmax(olevel *L) {
+  const long n = L->n;
+  double *r = L->r, *z = L->s, *p = L->d, *q = L->t;
+  double al[ORC_EIG_STEPS], be[ORC_EIG_STEPS], d[ORC_EIG_STEPS], e[ORC_EIG_STEPS];
+  for (long i = 0; i < n; ++i) r[i] = uniform01(ORC_EIG_SEED, 3, (uint64_t)i) - 0.5;
+  for (long i = 0; i < n; ++i) z[i] = r[i] / L->diag[i];
+  memcpy(p, z, sizeof(double) * n);
+  double rz = dot(n, r, z);
+  int m = 0;
+  for (int j = 0; j < ORC_EIG_STEPS && (long)j < n; ++j) {
+    spmv(L, p, q);
+    const double pq = dot(n, p, q);
+    if (!(pq > 0.0) || !(rz > 0.0)) break;
+    al[j] = rz / pq;
+    for (long i = 0; i < n; ++i) r[i] -= al[j] * q[i];
+    for (long i = 0; i < n; ++i) z[i] = r[i] / L->diag[i];
+    const double rz_new = dot(n, r, z);
+    be[j] = rz_new / rz;
+    for (long i = 0; i < n; ++i) p[i] = z[i] + be[j] * p[i];
+    rz = rz_new;
+    m = j + 1;
+  }
+  if (m == 0) return 2.0;
+  for (int j = 0; j < m; ++j) {
+    d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < m) e[j] = sqrt(be[j]) / al[j];
+  }
+  double lo = d[0], hi = d[0];
+  for (int j = 0; j < m; ++j) {
+    const double rad = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j + 1 < m ? fabs(e[j]) : 0.0);
+    if (d[j] - rad < lo) lo = d[j] - rad;
+    if (d[j] + rad > hi) hi = d[j] + rad;
+  }
+  for (int it = 0; it < 200; ++it) { /* largest: count below x is m - 1 */
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_below(m, d, e, mid) >= m) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
+
 /* ------------------------------------------------------------ smoother */
 /* One sweep of degree-m Chebyshev iteration for D^-1 A on [alpha, beta]
  * (preconditioned Chebyshev recurrence, Saad, Iterative Methods for Sparse
@@ -560,6 +638,34 @@ void *orc_create(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pr
 
 /* Upper end of level l's Chebyshev interval. */
 double orc_level_beta(void *hh, int l) { return ((ohier *)hh)->lv[l].beta; }
+double orc_level_alpha(void *hh, int l) { return ((ohier *)hh)->lv[l].alpha; }
+
+/* Chebyshev intervals: mode 0 keeps [eig_lo_frac beta, beta] with beta =
+ * eig_hi (Gershgorin on Galerkin levels); mode 1 sets
+ * [eig_lo_frac lambda, safety lambda] per level from the Lanczos estimate
+ * lambda of the largest eigenvalue of D^-1 A (the PETSc default is an
+ * estimate of this kind with the interval [0.1 lambda, 1.1 lambda]). */
+int orc_set_eig_mode(void *hh, int mode, double safety) {
+  ohier *H = (ohier *)hh;
+  if (!H || mode < 0 || mode > 1 || !(safety > 0.0)) return -1;
+  const double lo_frac = H->alpha / H->beta;
+  H->eig_mode = mode;
+  for (int l = 0; l < H->L; ++l) {
+    olevel *L = &H->lv[l];
+    if (mode == 1) {
+      const double lm = lanczos_lmax(L);
+      L->beta = safety * lm;
+      L->alpha = lo_frac * lm;
+    } else {
+      L->beta = (l > 0 && H->galerkin) ? gershgorin(L) : H->beta;
+      L->alpha = lo_frac * L->beta;
+    }
+  }
+  return 0;
+}
+
+/* Largest-eigenvalue estimate of level l (the Lanczos procedure above). */
+double orc_level_lanczos(void *hh, int l) { return lanczos_lmax(&((ohier *)hh)->lv[l]); }
 
 void orc_free(void *hh) {
   ohier *H = (ohier *)hh;

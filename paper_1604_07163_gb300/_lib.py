@@ -17,7 +17,7 @@ PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16k": 2}
 # every symbol include/mg.h declares
 EXPORTS = [
     "mg_params_default", "mg_setup", "mg_set_stream", "mg_solve", "mg_solve_adjoint", "mg_free", "mg_last_error",
-    "mg_num_levels", "mg_level_dims", "mg_history", "mg_apply", "mg_smooth", "mg_residual_restrict",
+    "mg_num_levels", "mg_level_dims", "mg_level_interval", "mg_history", "mg_apply", "mg_smooth", "mg_residual_restrict",
     "mg_prolong_add", "mg_coarse_solve", "mg_vcycle", "mg_gradient", "mg_residual_norm", "mg_timing_enable",
     "mg_timing_read", "mg_residual_norm_noalloc",
 ]
@@ -33,7 +33,7 @@ class MgParams(C.Structure):
         ("maxit", C.c_int), ("nonzero_guess", C.c_int), ("flexible", C.c_int), ("telescope_max_n", C.c_int),
         ("use_graph", C.c_int), ("stencil_kernel", C.c_int), ("use_pdl", C.c_int),
         ("smoother", C.c_int), ("richardson_omega", C.c_double), ("coarse_op", C.c_int),
-        ("krylov", C.c_int), ("gmres_restart", C.c_int),
+        ("krylov", C.c_int), ("gmres_restart", C.c_int), ("eig_mode", C.c_int), ("eig_safety", C.c_double),
     ]
 
 
@@ -74,6 +74,7 @@ def load():
         "mg_last_error": ([vp], C.c_char_p),
         "mg_num_levels": ([vp], i),
         "mg_level_dims": ([vp, i, P(C.c_int)], i),
+        "mg_level_interval": ([vp, i, P(C.c_double), P(C.c_double)], i),
         "mg_history": ([vp, P(C.c_double), i], i),
         "mg_apply": ([vp, i, vp, vp], i),
         "mg_smooth": ([vp, i, vp, vp, i], i),

@@ -49,7 +49,8 @@ struct LevelBuf {
   double* w64 = nullptr;
   void* dg = nullptr;
   double* dg64 = nullptr;
-  double beta = 2.0;  // upper end of the level's Chebyshev interval for D^-1 A
+  double beta = 2.0;   // Chebyshev interval [alpha, beta] of the level's D^-1 A
+  double alpha = 0.2;
 };
 
 std::string g_setup_error;
@@ -397,13 +398,13 @@ int level_result_cur(const mg_params& p) {
   return f & 1;
 }
 
-void cheb_consts(const mg_params& p, double beta_l, double* theta, double* delta, double* sigma) {
+void cheb_consts(const mg_params& p, double beta_l, double alpha_l, double* theta, double* delta, double* sigma) {
   if (p.smoother == MG_SMOOTHER_RICHARDSON) {  // one step x += omega D^-1 (b - A x) per sweep
     *theta = 1.0 / p.richardson_omega;
     *delta = *sigma = 0.0;
     return;
   }
-  const double beta = beta_l, alpha = p.eig_lo_frac * beta_l;
+  const double beta = beta_l, alpha = alpha_l;
   *theta = 0.5 * (beta + alpha);
   *delta = 0.5 * (beta - alpha);
   *sigma = *theta / *delta;
@@ -411,9 +412,9 @@ void cheb_consts(const mg_params& p, double beta_l, double* theta, double* delta
 
 // Coefficients of the Chebyshev steps j = 1..degree-1 (the same for every
 // sweep: the recurrence always restarts from rho_0 = 1/sigma), and 1/theta.
-void cheb_table(const mg_params& p, double beta_l, double* inv_theta, double* c1, double* c2) {
+void cheb_table(const mg_params& p, double beta_l, double alpha_l, double* inv_theta, double* c1, double* c2) {
   double theta, delta, sigma;
-  cheb_consts(p, beta_l, &theta, &delta, &sigma);
+  cheb_consts(p, beta_l, alpha_l, &theta, &delta, &sigma);
   *inv_theta = 1.0 / theta;
   double rho_prev = 1.0 / sigma;
   c1[0] = c2[0] = 0.0;
@@ -424,6 +425,8 @@ void cheb_table(const mg_params& p, double beta_l, double* inv_theta, double* c1
     rho_prev = rho;
   }
 }
+
+mg_status read_scal(mg_handle* h);
 
 template <class TV, class TC> struct Impl {
   using TVt = TV;
@@ -553,7 +556,7 @@ template <class TV, class TC> struct Impl {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
     double theta, delta, sigma;
-    cheb_consts(p, Lv.beta, &theta, &delta, &sigma);
+    cheb_consts(p, Lv.beta, Lv.alpha, &theta, &delta, &sigma);
     const TV inv_theta = (TV)(1.0 / theta);
     for (int j = j_from; j < p.cheby_degree; ++j) {
       double c1 = 0.0, c2 = 0.0;
@@ -608,7 +611,7 @@ template <class TV, class TC> struct Impl {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
     double theta, delta, sigma;
-    cheb_consts(p, Lv.beta, &theta, &delta, &sigma);
+    cheb_consts(p, Lv.beta, Lv.alpha, &theta, &delta, &sigma);
     const TV inv_theta = (TV)(1.0 / theta);
     if (!zero) return cheb_steps(h, l, cur, 0, 1.0 / sigma, fuse_rz);
     if (p.cheby_degree == 1) {
@@ -649,7 +652,7 @@ template <class TV, class TC> struct Impl {
     const bool single_step_dot = fuse_rz && p.nu_post == 1 && p.cheby_degree == 1;
     if ((Lv.zs || Lv.zs_prolong) && p.nu_post >= 1 && !single_step_dot) {
       double theta, delta, sigma;
-      cheb_consts(p, Lv.beta, &theta, &delta, &sigma);
+      cheb_consts(p, Lv.beta, Lv.alpha, &theta, &delta, &sigma);
       zs_launch(h, l, PolProlongStep0<TV, TV, TC>{Cv.g, V(Lv.x[cur]), V(Cv.x[ccur]), V(Lv.b), V(Lv.dinv),
                                                   V(Lv.x[cur ^ 1]), p.cheby_degree > 1 ? V(Lv.d) : nullptr,
                                                   C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(1.0 / theta)},
@@ -682,7 +685,7 @@ template <class TV, class TC> struct Impl {
       B.kz = C(Lv.kz);
       B.w = Lv.g27 ? C(Lv.w) : nullptr;
       B.dg = Lv.g27 ? V(Lv.dg) : nullptr;
-      cheb_table(h->prm, Lv.beta, &B.inv_theta, B.c1, B.c2);
+      cheb_table(h->prm, Lv.beta, Lv.alpha, &B.inv_theta, B.c1, B.c2);
     }
     a.nu_pre = h->prm.nu_pre;
     a.nu_post = h->prm.nu_post;
@@ -745,6 +748,87 @@ template <class TV, class TC> struct Impl {
       finish(h, nb, FIN_RZ);
     }
     return V(L0.x[zc]);
+  }
+
+  // Largest eigenvalue of D^-1 A on level l: CG with the Jacobi preconditioner
+  // for 10 steps from a seeded random right-hand side, in the V-cycle
+  // precision; the CG coefficients give the Lanczos tridiagonal matrix
+  // (T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_{j,j+1} = sqrt(b_j)/a_j), whose largest
+  // eigenvalue is found by bisection on Sturm counts.  Runs at setup in the
+  // level's work vectors.
+  static mg_status lanczos(mg_handle* h, int l, double* lmax) {
+    LevelBuf& Lv = h->lv[l];
+    const Geom& g = Lv.g;
+    const i64 n = g.len;
+    TV *r = V(Lv.r), *z = V(Lv.d), *p = V(Lv.x[0]), *q = V(Lv.x[1]);
+    const TV* dinv = V(Lv.dinv);
+    const int lb = lin_blocks(h, n);
+    mg_status s;
+    auto dot = [&](const TV* a, const TV* b, double* out) -> mg_status {
+      const int nb = linear<true>(h, n, LinDotT<TV>{a, b});
+      finish(h, nb, FIN_BB);
+      mg_status st = read_scal(h);
+      *out = h->hsc->bb;
+      return st;
+    };
+    k_lz_fill<TV><<<lin_blocks(h, g.npts()), 256, 0, h->s>>>(r, g, 20160424ull);
+    k_lz_jacobi<TV><<<lb, 256, 0, h->s>>>(z, r, dinv, n);
+    CK(cudaMemcpyAsync(p, z, (size_t)n * sizeof(TV), cudaMemcpyDeviceToDevice, h->s));
+    double rz;
+    if ((s = dot(r, z, &rz)) != MG_OK) return s;
+    double a[10], b[10];
+    int m = 0;
+    for (int j = 0; j < 10 && j < g.npts(); ++j) {
+      if (Lv.g27) zmarch<false>(h, g, OpApply27<TV, TV, TC>{p, q, C(Lv.w), g.len, V(Lv.dg)});
+      else zmarch<false>(h, g, OpApply<TV, TV, TC>{p, q, C(Lv.kx), C(Lv.ky), C(Lv.kz)});
+      double pq;
+      if ((s = dot(p, q, &pq)) != MG_OK) return s;
+      if (!(pq > 0.0) || !(rz > 0.0)) break;
+      a[j] = rz / pq;
+      k_lz_axpy<TV><<<lb, 256, 0, h->s>>>(r, q, -a[j], n);
+      k_lz_jacobi<TV><<<lb, 256, 0, h->s>>>(z, r, dinv, n);
+      double rz_new;
+      if ((s = dot(r, z, &rz_new)) != MG_OK) return s;
+      b[j] = rz_new / rz;
+      k_lz_xpay<TV><<<lb, 256, 0, h->s>>>(p, z, b[j], n);
+      rz = rz_new;
+      m = j + 1;
+    }
+    CKL();
+    if (m == 0) {
+      *lmax = 2.0;
+      return MG_OK;
+    }
+    double d[10], e[10];
+    for (int j = 0; j < m; ++j) {
+      d[j] = 1.0 / a[j] + (j > 0 ? b[j - 1] / a[j - 1] : 0.0);
+      e[j] = j + 1 < m ? std::sqrt(b[j]) / a[j] : 0.0;
+    }
+    // Gershgorin bracket, then bisection on the number of eigenvalues below x
+    double lo = d[0], hi = d[0];
+    for (int j = 0; j < m; ++j) {
+      const double rad = std::fabs(e[j]) + (j > 0 ? std::fabs(e[j - 1]) : 0.0);
+      lo = std::min(lo, d[j] - rad);
+      hi = std::max(hi, d[j] + rad);
+    }
+    auto below = [&](double x) {
+      int c = 0;
+      double piv = 1.0;
+      for (int j = 0; j < m; ++j) {
+        piv = d[j] - x - (j > 0 ? e[j - 1] * e[j - 1] / piv : 0.0);
+        if (piv == 0.0) piv = -1e-300;
+        c += piv < 0.0;
+      }
+      return c;
+    };
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (below(mid) >= m) hi = mid;
+      else lo = mid;
+    }
+    *lmax = hi;
+    return MG_OK;
   }
 
   // float32 copy of the float64 residual as the V-cycle's finest right-hand side
@@ -1054,6 +1138,20 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   }
   AL(h->partials, double, 2 * (i64)h->pstride);
   AL(h->dsc, Scal, 1);
+  // Chebyshev intervals: the fixed (or Gershgorin) one, or the Lanczos estimate
+  for (int l = 0; l < L; ++l) {
+    LevelBuf& Lv = h->lv[l];
+    if (p.eig_mode == 1) {
+      double lm = 2.0;
+      const mg_status se = dispatch(h, [&](auto impl) { return decltype(impl)::lanczos(h, l, &lm); });
+      if (se != MG_OK) return se;
+      if (!(lm > 0.0) || !std::isfinite(lm)) return fail(h, MG_ERR_NONFINITE, "eigenvalue estimate failed");
+      Lv.beta = p.eig_safety * lm;
+      Lv.alpha = p.eig_lo_frac * lm;
+    } else {
+      Lv.alpha = p.eig_lo_frac * Lv.beta;
+    }
+  }
   // coarsest operator: dense float64 assembly and Cholesky factorisation
   AL(h->Lc, double, (i64)h->nc * h->nc);
   const LevelBuf& Cv = h->lv[L - 1];
@@ -1463,6 +1561,8 @@ mg_status mg_params_default(mg_params* p) {
   p->coarse_op = MG_COARSE_REDISCRETISED;
   p->krylov = MG_KRYLOV_CG;
   p->gmres_restart = 30;
+  p->eig_mode = 0;
+  p->eig_safety = 1.1;
   return MG_OK;
 }
 
@@ -1481,7 +1581,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 4 ||
       p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0) ||
       p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN || p.krylov < MG_KRYLOV_CG ||
-      p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256)
+      p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256 || p.eig_mode < 0 ||
+      p.eig_mode > 1 || !(p.eig_safety > 0.0))
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible
@@ -1577,6 +1678,13 @@ int mg_num_levels(const mg_handle* h) { return h ? h->L : 0; }
 mg_status mg_level_dims(const mg_handle* h, int l, int* N3) {
   if (!h || !N3 || l < 0 || l >= h->L) return MG_ERR_ARG;
   for (int a = 0; a < 3; ++a) N3[a] = h->lv[l].N[a];
+  return MG_OK;
+}
+
+mg_status mg_level_interval(const mg_handle* h, int l, double* alpha, double* beta) {
+  if (!h || !alpha || !beta || l < 0 || l >= h->L) return MG_ERR_ARG;
+  *alpha = h->lv[l].alpha;
+  *beta = h->lv[l].beta;
   return MG_OK;
 }
 

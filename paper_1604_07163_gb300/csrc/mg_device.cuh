@@ -465,6 +465,20 @@ template <class TZ, bool FLEX, bool B32> struct LinCgUpd {
   }
 };
 
+// acc0 += a.b for two vectors of the same (V-cycle) precision
+template <class TA> struct LinDotT {
+  const TA* a;
+  const TA* b;
+  __device__ void prepare() {}
+  __device__ __forceinline__ void pt4(i64 t, double& a0, double&) const {
+    double av[4], bv[4];
+    ld4(a + t, av);
+    ld4(b + t, bv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a0 = fma(av[u], bv[u], a0);
+  }
+};
+
 // acc0 += a.b
 template <class TB> struct LinDot {
   const double* a;

@@ -285,6 +285,43 @@ __global__ void k_trinv(const double* L, double* Li, int n) {
   }
 }
 
+// ------------------------------------------------------------ eigenvalue estimate
+// Counter-based uniform numbers in [0,1) from Vigna's SplitMix64 finaliser:
+// u(seed, stream, idx) = (sm(sm(seed ^ stream << 56) ^ idx) >> 11) * 2^-53.
+__host__ __device__ __forceinline__ unsigned long long sm64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ double u01(unsigned long long seed, unsigned long long stream,
+                                               unsigned long long idx) {
+  return (double)(sm64(sm64(seed ^ (stream << 56)) ^ idx) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Start vector of the Lanczos estimate: u - 1/2 at every interior point
+// (stream 3, index = interior point number (k ny + j) nx + i); pads stay zero.
+template <class TV> __global__ void k_lz_fill(TV* r, Geom g, unsigned long long seed) {
+  const i64 n = g.npts();
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((i64)g.nx * g.ny));
+    r[g.at(i, j, k)] = store_as<TV>(u01(seed, 3, (unsigned long long)t) - 0.5);
+  }
+}
+// z = D^-1 r;  y += a x;  y = x + b y  over whole padded arrays (pads stay zero)
+template <class TV> __global__ void k_lz_jacobi(TV* z, const TV* r, const TV* dinv, i64 n) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    z[t] = store_as<TV>(cvt<double>(dinv[t]) * cvt<double>(r[t]));
+}
+template <class TV> __global__ void k_lz_axpy(TV* y, const TV* x, double a, i64 n) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    y[t] = store_as<TV>(fma(a, cvt<double>(x[t]), cvt<double>(y[t])));
+}
+template <class TV> __global__ void k_lz_xpay(TV* y, const TV* x, double b, i64 n) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    y[t] = store_as<TV>(fma(b, cvt<double>(y[t]), cvt<double>(x[t])));
+}
+
 // ------------------------------------------------------------ scalars
 enum FinishMode { FIN_BB = 0, FIN_RR = 1, FIN_RZ0 = 2, FIN_PQ = 3, FIN_RZ = 4, FIN_TRUE = 5 };
 

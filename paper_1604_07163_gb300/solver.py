@@ -38,6 +38,8 @@ class Params:
     coarse_op: str = "rediscretised"  # or "galerkin" (R A P, 27-point coarse stencils)
     krylov: str = "cg"  # or "fgmres" (flexible GMRES(gmres_restart), right-preconditioned)
     gmres_restart: int = 30
+    eig_mode: int = 0  # 1: per-level Chebyshev interval from a 10-step Lanczos estimate
+    eig_safety: float = 1.1
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -50,6 +52,8 @@ class Params:
         p.coarse_op = {"rediscretised": 0, "galerkin": 1}[self.coarse_op]
         p.krylov = {"cg": 0, "fgmres": 1}[self.krylov]
         p.gmres_restart = self.gmres_restart
+        p.eig_mode = self.eig_mode
+        p.eig_safety = self.eig_safety
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p
@@ -150,6 +154,12 @@ class MGSolver:
         N = (C.c_int * 3)()
         self._check(self._lib.mg_level_dims(self._h, l, N))
         return (N[2], N[1], N[0])
+
+    def level_interval(self, l: int):
+        """(alpha, beta): the Chebyshev interval of D^-1 A on level l."""
+        a, b = C.c_double(), C.c_double()
+        self._check(self._lib.mg_level_interval(self._h, l, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def history(self):
         n = self._lib.mg_history(self._h, None, 0)

@@ -47,6 +47,7 @@ CASES = [
     ((17, 9, 17), 2, 1.0, dict(smoother="richardson", richardson_omega=1.0, nu_pre=2, nu_post=3)),
     ((17, 17, 33), 4, 3.0, dict(coarse_op="galerkin")),  # Galerkin R A P coarse operators
     ((33, 17, 17), 2, 2.0, dict(coarse_op="galerkin", cheby_degree=3, face_rule=1)),
+    ((17, 17, 33), 4, 2.0, dict(eig_mode=1)),  # Lanczos eigenvalue estimate per level
 ]
 
 
@@ -57,7 +58,8 @@ def oracle_for(k, params):
                          coarse_rule=op.get("coarse_k_rule", 0), face_rule=op.get("face_rule", 0),
                          smoother=1 if op.get("smoother") == "richardson" else 0,
                          omega=op.get("richardson_omega", 6.0 / 7.0),
-                         galerkin=op.get("coarse_op") == "galerkin")
+                         galerkin=op.get("coarse_op") == "galerkin", eig_mode=op.get("eig_mode", 0),
+                         eig_safety=op.get("eig_safety", 1.1))
 
 
 def make(dims, block, rng, params, seed=101):
@@ -234,6 +236,30 @@ def test_fgmres_solve_parity(gpu_lib, params):
     assert st32.iters <= ito + 3
     h = np.asarray(st.history)
     assert np.all(np.diff(h[1:]) <= 1e-15 + 1e-12 * h[1:-1])  # non-increasing within each cycle's estimate
+
+
+@pytest.mark.parametrize("params", [dict(eig_mode=1), dict(eig_mode=1, coarse_op="galerkin", eig_safety=1.2)])
+def test_lanczos_intervals_and_solve_parity(gpu_lib, params):
+    """eig_mode 1: every level's Chebyshev interval from the GPU's Lanczos
+    estimate equals the oracle's (same seeded start vector; only rounding
+    order differs), and the solve takes the oracle's iteration count."""
+    import paper_1604_07163_gb300 as mg
+    dims = (65, 65, 65)
+    k = mi.cell_k(dims, 8, -2.0, 2.0, 83)
+    f = mi.rhs_f(dims, 83)
+    O = oracle_for(k, params)
+    S = mg.MGSolver(T(k), mg.Params(maxit=400, **params))
+    for l in range(O.levels):
+        a, b = S.level_interval(l)
+        assert abs(b - O.level_beta(l)) <= 1e-11 * b, (l, b, O.level_beta(l))
+        assert abs(a - O.level_alpha(l)) <= 1e-11 * a
+    xo, ito, _ = O.pcg(f, 1e-10, maxit=400)
+    x, st = S.solve(T(f), 1e-10)
+    assert abs(st.iters - ito) <= 1
+    assert rel2(N(x), xo) < 1e-9
+    S32 = mg.MGSolver(T(k), mg.Params(maxit=400, precision="mixed_fp32", **params))
+    for l in range(O.levels):
+        assert abs(S32.level_interval(l)[1] - O.level_beta(l)) <= 1e-4 * O.level_beta(l)  # float32 Lanczos
 
 
 def test_fixed_iteration_parity_and_not_converged(gpu_lib):

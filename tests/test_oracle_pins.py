@@ -449,6 +449,51 @@ def test_fgmres_exact_preconditioner_and_agreement_with_cg():
         assert np.linalg.norm(x - xc) <= 1e-9 * np.linalg.norm(xc)
 
 
+# ------------------------------------------------------------------ eigenvalue estimate
+def test_lanczos_estimate_matches_numpy_and_bounds_the_spectrum():
+    """eig_mode 1: the Lanczos estimate of the largest eigenvalue of D^-1 A
+    equals the one built here with numpy (10 steps of Jacobi-preconditioned CG
+    from the seeded start vector u(20160424, 3, i) - 1/2, the Lanczos
+    tridiagonal from the CG coefficients, numpy's eigvalsh), lies below the
+    true largest eigenvalue (a Ritz value) and close to it; the level's
+    Chebyshev interval becomes [0.1 L, 1.1 L]."""
+    dims = (17, 17, 33)
+    k = mi.cell_k(dims, 4, -2, 2, seed=61)
+    O = oracle.Oracle(k, eig_mode=1)
+    for l in range(O.levels - 1):
+        A = dense_A(O, l).toarray()
+        n = A.shape[0]
+        D = np.diag(A)
+        r = mi.uniform(20160424, 3, np.arange(n, dtype=np.uint64)) - 0.5
+        z = r / D
+        p = z.copy()
+        rz = r @ z
+        al, be = [], []
+        for _ in range(min(10, n)):
+            q = A @ p
+            a = rz / (p @ q)
+            r = r - a * q
+            z = r / D
+            rzn = r @ z
+            al.append(a)
+            be.append(rzn / rz)
+            p = z + be[-1] * p
+            rz = rzn
+        m = len(al)
+        Tm = np.zeros((m, m))
+        for j in range(m):
+            Tm[j, j] = 1 / al[j] + (be[j - 1] / al[j - 1] if j else 0.0)
+            if j + 1 < m:
+                Tm[j, j + 1] = Tm[j + 1, j] = np.sqrt(be[j]) / al[j]
+        ref = np.max(np.linalg.eigvalsh(Tm))
+        got = O.level_lanczos(l)
+        assert abs(got - ref) <= 1e-10 * ref, (l, got, ref)
+        lmax = np.max(np.linalg.eigvalsh(A / np.sqrt(np.outer(D, D))))
+        assert 0.8 * lmax <= got <= lmax * (1 + 1e-12)
+        assert abs(O.level_beta(l) - 1.1 * got) <= 1e-14 * got
+        assert abs(O.level_alpha(l) - 0.1 * got) <= 1e-14 * got
+
+
 # ------------------------------------------------------------------ transfers
 def test_prolongation_exact_on_trilinear_functions():
     dims = (17, 17, 17)
