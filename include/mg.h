@@ -124,6 +124,12 @@ typedef struct {
                           a 10-step CG-Lanczos estimate of the largest eigenvalue of D^-1 A on the level,
                           from a seeded random right-hand side (computed at setup) */
   double eig_safety;   /* upper factor of eig_mode 1 (default 1.1) */
+  int coarse_solve;    /* coarsest solve: 0 (default) dense Cholesky; 1 GMRES preconditioned with
+                          Jacobi, stopped at coarse_rtol (the inexact, truncated coarse solve of Sec. 5;
+                          the V-cycle is then no longer a fixed linear operator: use MG_KRYLOV_FGMRES).
+                          1 needs a coarsest level of at most 32 unknowns */
+  double coarse_rtol;  /* relative residual of the inexact coarse solve (default 1e-4) */
+  int coarse_maxit;    /* its iteration limit, 1..32 (default 30) */
 } mg_params;
 
 typedef struct {

@@ -58,6 +58,8 @@ def _load():
         lib.orc_level_alpha.argtypes = [vp, C.c_int]
         lib.orc_level_lanczos.restype = C.c_double
         lib.orc_level_lanczos.argtypes = [vp, C.c_int]
+        lib.orc_set_coarse.restype = C.c_int
+        lib.orc_set_coarse.argtypes = [vp, C.c_int, C.c_double, C.c_int]
         lib.orc_set_eig_mode.restype = C.c_int
         lib.orc_set_eig_mode.argtypes = [vp, C.c_int, C.c_double]
         lib.orc_free.argtypes = [vp]
@@ -102,12 +104,14 @@ class Oracle:
     def __init__(self, k_cells, levels: int | None = None, nu_pre: int = 1, nu_post: int = 1,
                  degree: int = 2, eig_lo_frac: float = 0.1, eig_hi: float = 2.0,
                  coarse_rule: int = 0, face_rule: int = 0, smoother: int = 0, omega: float = 6.0 / 7.0,
-                 galerkin: bool = False, eig_mode: int = 0, eig_safety: float = 1.1):
+                 galerkin: bool = False, eig_mode: int = 0, eig_safety: float = 1.1, coarse_gmres: bool = False,
+                 coarse_rtol: float = 1e-4, coarse_maxit: int = 30):
         """smoother 0: Chebyshev(degree)-Jacobi sweeps; 1: Richardson-Jacobi
         iterations x += omega D^-1 (b - A x), nu_pre / nu_post of them.
         galerkin: coarse operators R A P instead of re-discretisation.
         eig_mode 1: per-level Chebyshev interval [eig_lo_frac L, eig_safety L]
-        from a 10-step Lanczos estimate L of the largest eigenvalue of D^-1 A."""
+        from a 10-step Lanczos estimate L of the largest eigenvalue of D^-1 A.
+        coarse_gmres: inexact coarsest solve, GMRES with Jacobi to coarse_rtol."""
         lib = _load()
         k = np.ascontiguousarray(k_cells, dtype=np.float64)
         self.dims = tuple(s + 1 for s in k.shape)
@@ -122,6 +126,8 @@ class Oracle:
             raise ValueError("oracle: invalid smoother")
         if eig_mode and lib.orc_set_eig_mode(self._h, eig_mode, eig_safety) != 0:
             raise ValueError("oracle: invalid eigenvalue-estimate mode")
+        if coarse_gmres and lib.orc_set_coarse(self._h, 1, coarse_rtol, coarse_maxit) != 0:
+            raise ValueError("oracle: invalid coarse-solve settings")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -70,6 +70,9 @@ typedef struct {
   int face_rule;       /* edge k: 0 harmonic, 1 arithmetic mean of the 4 cells */
   int galerkin;        /* coarse operators: 0 re-discretised, 1 Galerkin R A P */
   int eig_mode;        /* Chebyshev interval: 0 fixed / Gershgorin, 1 Lanczos estimate */
+  int coarse_mode;     /* coarsest solve: 0 Cholesky, 1 GMRES with Jacobi to coarse_rtol */
+  double coarse_rtol;
+  int coarse_maxit;
   double *Ac, *Lc;     /* dense coarsest operator and its Cholesky factor */
 } ohier;
 
@@ -498,7 +501,82 @@ static int build_coarse(ohier *H) {
   return 0;
 }
 
+/* Inexact coarsest solve (the "truncated" coarse solve of Sec. 5): GMRES
+ * preconditioned on the right with Jacobi (the diagonal of A_L), classical
+ * Gram-Schmidt, Givens rotations, from x = 0, stopped when the rotated
+ * residual norm falls to coarse_rtol times ||b|| or after coarse_maxit steps. */
+static void coarse_gmres(const ohier *H, const double *b, double *x) {
+  const int n = H->nc, m = H->coarse_maxit;
+  const double *A = H->Ac;
+  double *V = (double *)calloc((size_t)(m + 1) * n, sizeof(double));
+  double *Hs = (double *)calloc((size_t)(m + 1) * m, sizeof(double));
+  double *w = (double *)malloc(sizeof(double) * n), *z = (double *)malloc(sizeof(double) * n);
+  double *g = (double *)calloc(m + 1, sizeof(double)), *cs = (double *)malloc(sizeof(double) * m);
+  double *sn = (double *)malloc(sizeof(double) * m), *y = (double *)malloc(sizeof(double) * m);
+  for (int i = 0; i < n; ++i) x[i] = 0.0;
+  double beta = 0.0;
+  for (int i = 0; i < n; ++i) beta += b[i] * b[i];
+  beta = sqrt(beta);
+  int jj = 0;
+  if (beta > 0.0) {
+    for (int i = 0; i < n; ++i) V[i] = b[i] / beta;
+    g[0] = beta;
+    for (int j = 0; j < m; ++j) {
+      for (int i = 0; i < n; ++i) z[i] = V[(size_t)j * n + i] / A[(size_t)i * n + i];
+      for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += A[(size_t)i * n + k] * z[k];
+        w[i] = s;
+      }
+      for (int i = 0; i <= j; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += w[k] * V[(size_t)i * n + k];
+        Hs[(size_t)i * m + j] = s;
+      }
+      for (int i = 0; i <= j; ++i)
+        for (int k = 0; k < n; ++k) w[k] -= Hs[(size_t)i * m + j] * V[(size_t)i * n + k];
+      double hn = 0.0;
+      for (int k = 0; k < n; ++k) hn += w[k] * w[k];
+      hn = sqrt(hn);
+      Hs[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0)
+        for (int k = 0; k < n; ++k) V[(size_t)(j + 1) * n + k] = w[k] / hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = Hs[(size_t)i * m + j], c = Hs[(size_t)(i + 1) * m + j];
+        Hs[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        Hs[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = Hs[(size_t)j * m + j], c = Hs[(size_t)(j + 1) * m + j];
+      const double d = sqrt(a * a + c * c);
+      if (!(d > 0.0)) break;
+      cs[j] = a / d;
+      sn[j] = c / d;
+      Hs[(size_t)j * m + j] = d;
+      Hs[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      jj = j + 1;
+      if (fabs(g[j + 1]) <= H->coarse_rtol * beta || hn == 0.0) break;
+    }
+    for (int i = jj - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < jj; ++k) s -= Hs[(size_t)i * m + k] * y[k];
+      y[i] = s / Hs[(size_t)i * m + i];
+    }
+    for (int i = 0; i < n; ++i) { /* x = D^-1 V y */
+      double s = 0.0;
+      for (int k = 0; k < jj; ++k) s += y[k] * V[(size_t)k * n + i];
+      x[i] = s / A[(size_t)i * n + i];
+    }
+  }
+  free(V); free(Hs); free(w); free(z); free(g); free(cs); free(sn); free(y);
+}
+
 static void coarse_solve(const ohier *H, const double *b, double *x) {
+  if (H->coarse_mode == 1) {
+    coarse_gmres(H, b, x);
+    return;
+  }
   int n = H->nc;
   const double *C = H->Lc;
   for (int i = 0; i < n; ++i) { /* L y = b */
@@ -634,6 +712,19 @@ void *orc_create(int Nx, int Ny, int Nz, const double *kc, int levels, int nu_pr
                  int degree, double eig_lo_frac, double eig_hi, int coarse_rule, int face_rule) {
   return orc_create_opt(Nx, Ny, Nz, kc, levels, nu_pre, nu_post, degree, eig_lo_frac, eig_hi, coarse_rule,
                         face_rule, 0);
+}
+
+/* Coarsest solve: mode 0 the Cholesky factorisation; mode 1 GMRES with the
+ * Jacobi preconditioner to rtol, at most maxit steps (an inexact solve: the
+ * preconditioner is then no longer a fixed linear operator, and the outer
+ * method should be flexible GMRES). */
+int orc_set_coarse(void *hh, int mode, double rtol, int maxit) {
+  ohier *H = (ohier *)hh;
+  if (!H || mode < 0 || mode > 1 || !(rtol > 0.0) || maxit < 1) return -1;
+  H->coarse_mode = mode;
+  H->coarse_rtol = rtol;
+  H->coarse_maxit = maxit;
+  return 0;
 }
 
 /* Upper end of level l's Chebyshev interval. */

@@ -34,6 +34,7 @@ class MgParams(C.Structure):
         ("use_graph", C.c_int), ("stencil_kernel", C.c_int), ("use_pdl", C.c_int),
         ("smoother", C.c_int), ("richardson_omega", C.c_double), ("coarse_op", C.c_int),
         ("krylov", C.c_int), ("gmres_restart", C.c_int), ("eig_mode", C.c_int), ("eig_safety", C.c_double),
+        ("coarse_solve", C.c_int), ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int),
     ]
 
 

@@ -67,6 +67,7 @@ struct mg_handle {
   LevelBuf lv[MG_MAX_LEVELS];
   double* Lc = nullptr;  // Cholesky factor of the coarsest operator
   double* Li = nullptr;  // its inverse and the transpose when the coarsest level has at most 32 unknowns
+  double* Ac = nullptr;  // the dense coarsest operator (inexact coarse solve)
   // flexible GMRES: basis V_0..V_m (float64), preconditioned Z_0..Z_{m-1}
   // (V-cycle precision), one column's dots and the coefficients y, partial sums
   double* kv = nullptr;
@@ -692,6 +693,9 @@ template <class TV, class TC> struct Impl {
     a.degree = h->prm.cheby_degree;
     a.Lc = h->Lc;
     a.Li = h->Li;
+    a.Ac = h->prm.coarse_solve == 1 ? h->Ac : nullptr;
+    a.coarse_rtol = h->prm.coarse_rtol;
+    a.coarse_maxit = h->prm.coarse_maxit;
     a.nc = h->nc;
     const int e = tm_begin(h, MG_K_BOTTOM, l0);
     launch(h, k_bottom<TV, TV, TC>, dim3(1), dim3(BOT_THREADS), 0, a);
@@ -1158,6 +1162,11 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   if (Cv.g27) k_assemble_dense27<<<lin_blocks(h, h->nc), 256, 0, h->s>>>(Cv.w64, Cv.dg64, Cv.g, h->Lc);
   else k_assemble_dense<<<lin_blocks(h, h->nc), 256, 0, h->s>>>(Cv.kx64, Cv.ky64, Cv.kz64, Cv.g, h->Lc);
   CKL();
+  if (p.coarse_solve == 1) {  // keep the operator for the inexact solve
+    if (h->nc > 32) return fail(h, MG_ERR_ARG, "the inexact coarse solve needs at most 32 coarsest unknowns");
+    AL(h->Ac, double, (i64)h->nc * h->nc);
+    CK(cudaMemcpyAsync(h->Ac, h->Lc, sizeof(double) * h->nc * h->nc, cudaMemcpyDeviceToDevice, h->s));
+  }
   CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s));
   k_cholesky<<<1, 1024, 0, h->s>>>(h->Lc, h->nc, h->dflag);
   CKL();
@@ -1563,6 +1572,9 @@ mg_status mg_params_default(mg_params* p) {
   p->gmres_restart = 30;
   p->eig_mode = 0;
   p->eig_safety = 1.1;
+  p->coarse_solve = 0;
+  p->coarse_rtol = 1e-4;
+  p->coarse_maxit = 30;
   return MG_OK;
 }
 
@@ -1582,7 +1594,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0) ||
       p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN || p.krylov < MG_KRYLOV_CG ||
       p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256 || p.eig_mode < 0 ||
-      p.eig_mode > 1 || !(p.eig_safety > 0.0))
+      p.eig_mode > 1 || !(p.eig_safety > 0.0) || p.coarse_solve < 0 || p.coarse_solve > 1 ||
+      !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible

@@ -461,6 +461,9 @@ template <class TV, class TC> struct BotArgs {
   int nu_pre, nu_post, degree;
   const double* Lc;    // Cholesky factor of the coarsest operator (n x n)
   const double* Li;    // its inverse, then the transpose (n <= 32), else null
+  const double* Ac;    // the coarsest operator itself (inexact solve), else null
+  double coarse_rtol;  // inexact solve: GMRES-Jacobi to this relative residual,
+  int coarse_maxit;    // at most this many steps (<= 32)
   int nc;
 };
 
@@ -509,8 +512,93 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
 // n <= 32 the two triangular solves are products with the precomputed L^-1:
 // a substitution is a chain of n dependent divisions and shuffles, slow on
 // GB300's float64 pipe.  Larger n substitute with the whole block.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Inexact coarsest solve (the truncated coarse solve of the paper's Sec. 5):
+// GMRES with the Jacobi preconditioner on the right, classical Gram-Schmidt,
+// Givens rotations, from zero, stopped when the rotated residual norm is at
+// most rtol ||b|| or after m (<= 32) steps.  One warp, lane i holding
+// component i (n <= 32); the Krylov basis and the Hessenberg columns live in
+// shared memory; lane 0 applies the rotations.  y holds b on entry and x on
+// exit.
+__device__ void warp_gmres(const double* A, int n, double rtol, int m, double* y) {
+  __shared__ double Vs[33 * 32], Hs[33 * 32], gs[33], cs[32], sn[32], ys[32];
+  __shared__ int jj_s;
+  const int lane = threadIdx.x;
+  const bool on = lane < n;
+  const double bi = on ? y[lane] : 0.0;
+  const double dl = on ? A[lane * n + lane] : 1.0;
+  const double beta = sqrt(warp_sum_d(bi * bi));
+  double xo = 0.0;
+  if (beta > 0.0) {
+    Vs[lane] = bi / beta;
+    if (lane == 0) {
+      for (int i = 0; i <= m; ++i) gs[i] = 0.0;
+      gs[0] = beta;
+      jj_s = 0;
+    }
+    __syncwarp();
+    for (int j = 0; j < m; ++j) {
+      const double z = on ? Vs[j * 32 + lane] / dl : 0.0;
+      double w = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double zk = __shfl_sync(0xffffffffu, z, k);
+        if (on) w = fma(A[lane * n + k], zk, w);
+      }
+      for (int i = 0; i <= j; ++i) {  // all coefficients from the same w
+        const double h = warp_sum_d(w * Vs[i * 32 + lane]);
+        if (lane == 0) Hs[i * 32 + j] = h;
+      }
+      __syncwarp();
+      for (int i = 0; i <= j; ++i) w -= Hs[i * 32 + j] * Vs[i * 32 + lane];
+      const double hn = sqrt(warp_sum_d(w * w));
+      if (hn > 0.0) Vs[(j + 1) * 32 + lane] = w / hn;
+      if (lane == 0) {
+        Hs[(j + 1) * 32 + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hs[i * 32 + j], c = Hs[(i + 1) * 32 + j];
+          Hs[i * 32 + j] = cs[i] * a + sn[i] * c;
+          Hs[(i + 1) * 32 + j] = -sn[i] * a + cs[i] * c;
+        }
+        const double a = Hs[j * 32 + j], c = Hs[(j + 1) * 32 + j];
+        const double d = sqrt(a * a + c * c);
+        if (d > 0.0) {
+          cs[j] = a / d;
+          sn[j] = c / d;
+          Hs[j * 32 + j] = d;
+          Hs[(j + 1) * 32 + j] = 0.0;
+          gs[j + 1] = -sn[j] * gs[j];
+          gs[j] = cs[j] * gs[j];
+          jj_s = j + 1;
+        }
+      }
+      __syncwarp();
+      if (jj_s != j + 1 || fabs(gs[j + 1]) <= rtol * beta || hn == 0.0) break;
+    }
+    if (lane == 0) {  // R y = g
+      const int jj = jj_s;
+      for (int i = jj - 1; i >= 0; --i) {
+        double v = gs[i];
+        for (int k = i + 1; k < jj; ++k) v -= Hs[i * 32 + k] * ys[k];
+        ys[i] = v / Hs[i * 32 + i];
+      }
+    }
+    __syncwarp();
+    double sacc = 0.0;
+    for (int k = 0; k < jj_s; ++k) sacc += ys[k] * Vs[k * 32 + lane];
+    xo = sacc / dl;
+  }
+  if (on) y[lane] = xo;
+  __syncwarp();
+}
+
 template <class TV>
-__device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, const double* Li, int n) {
+__device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, const double* Li, int n,
+                                 const double* Ac = nullptr, double crtol = 0.0, int cmaxit = 0) {
   __shared__ double y[1024];
   __shared__ double t[32];
   for (int u = threadIdx.x; u < n; u += blockDim.x) {
@@ -518,7 +606,9 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
     y[u] = cvt<double>(b[g.at(i, j, k)]);
   }
   __syncthreads();
-  if (n <= 32 && Li) {
+  if (Ac && n <= 32) {
+    if (threadIdx.x < 32) warp_gmres(Ac, n, crtol, cmaxit, y);
+  } else if (n <= 32 && Li) {
     // one warp: lane w forms row w of each product with n multiply-adds (the
     // float64 pipe issues per warp instruction, so one warp of n steps costs
     // less than n warps of shuffle-tree sums)
@@ -612,7 +702,8 @@ __global__ void __launch_bounds__(BOT_THREADS) k_bottom(const __grid_constant__ 
     block_for(rs, a.lv[l + 1].g);
     __syncthreads();
   }
-  bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.Li, a.nc);
+  bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.Li, a.nc, a.Ac, a.coarse_rtol,
+                       a.coarse_maxit);
   cur[L - 1] = 0;
   for (int l = L - 2; l >= 0; --l) {
     const BotLevel<TV, TC>& V = a.lv[l];

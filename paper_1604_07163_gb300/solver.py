@@ -40,6 +40,9 @@ class Params:
     gmres_restart: int = 30
     eig_mode: int = 0  # 1: per-level Chebyshev interval from a 10-step Lanczos estimate
     eig_safety: float = 1.1
+    coarse_solve: str = "cholesky"  # or "gmres" (Jacobi-preconditioned, to coarse_rtol; use krylov="fgmres")
+    coarse_rtol: float = 1e-4
+    coarse_maxit: int = 30
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -54,6 +57,9 @@ class Params:
         p.gmres_restart = self.gmres_restart
         p.eig_mode = self.eig_mode
         p.eig_safety = self.eig_safety
+        p.coarse_solve = {"cholesky": 0, "gmres": 1}[self.coarse_solve]
+        p.coarse_rtol = self.coarse_rtol
+        p.coarse_maxit = self.coarse_maxit
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p

@@ -48,6 +48,7 @@ CASES = [
     ((17, 17, 33), 4, 3.0, dict(coarse_op="galerkin")),  # Galerkin R A P coarse operators
     ((33, 17, 17), 2, 2.0, dict(coarse_op="galerkin", cheby_degree=3, face_rule=1)),
     ((17, 17, 33), 4, 2.0, dict(eig_mode=1)),  # Lanczos eigenvalue estimate per level
+    ((17, 17, 17), 4, 2.0, dict(coarse_solve="gmres")),  # inexact GMRES-Jacobi coarse solve
 ]
 
 
@@ -59,7 +60,8 @@ def oracle_for(k, params):
                          smoother=1 if op.get("smoother") == "richardson" else 0,
                          omega=op.get("richardson_omega", 6.0 / 7.0),
                          galerkin=op.get("coarse_op") == "galerkin", eig_mode=op.get("eig_mode", 0),
-                         eig_safety=op.get("eig_safety", 1.1))
+                         eig_safety=op.get("eig_safety", 1.1), coarse_gmres=op.get("coarse_solve") == "gmres",
+                         coarse_rtol=op.get("coarse_rtol", 1e-4), coarse_maxit=op.get("coarse_maxit", 30))
 
 
 def make(dims, block, rng, params, seed=101):
@@ -214,7 +216,9 @@ def test_galerkin_solve_parity_high_contrast(gpu_lib, precision):
 
 
 @pytest.mark.parametrize("params", [dict(), dict(gmres_restart=5),
-                                    dict(coarse_op="galerkin", smoother="richardson", nu_pre=8, nu_post=8)])
+                                    dict(coarse_op="galerkin", smoother="richardson", nu_pre=8, nu_post=8),
+                                    dict(coarse_op="galerkin", smoother="richardson", nu_pre=8, nu_post=8,
+                                         coarse_solve="gmres")])
 def test_fgmres_solve_parity(gpu_lib, params):
     """Flexible GMRES right-preconditioned by the V-cycle (the paper's outer
     method in Sec. 5; the last case is its configuration: Galerkin coarse

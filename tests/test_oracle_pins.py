@@ -449,6 +449,31 @@ def test_fgmres_exact_preconditioner_and_agreement_with_cg():
         assert np.linalg.norm(x - xc) <= 1e-9 * np.linalg.norm(xc)
 
 
+# ------------------------------------------------------------------ inexact coarse solve
+def test_coarse_gmres_is_exact_in_n_steps_and_meets_its_tolerance():
+    """GMRES on the n coarsest unknowns reproduces the exact (Cholesky / numpy)
+    solve when allowed n steps and a tiny tolerance; with the truncated
+    tolerance 1e-4 of Sec. 5 its true residual is at most 1e-4 ||b|| (the
+    rotated residual norm equals the true one in exact arithmetic)."""
+    dims = (17, 9, 17)
+    k = mi.cell_k(dims, 2, -2, 2, seed=71)
+    Oe = oracle.Oracle(k)
+    L = Oe.levels - 1
+    dc = Oe.level_dims(L)
+    b = mi.random_nodal(dc, 4)
+    A = dense_A(Oe, L).toarray()
+    n = A.shape[0]
+    x_np = np.linalg.solve(A, interior(b).ravel())
+    Ox = oracle.Oracle(k, coarse_gmres=True, coarse_rtol=1e-14, coarse_maxit=n)
+    x = interior(Ox.coarse_solve(b)).ravel()
+    assert np.linalg.norm(x - x_np) <= 1e-10 * np.linalg.norm(x_np)
+    Ot = oracle.Oracle(k, coarse_gmres=True)
+    xt = interior(Ot.coarse_solve(b)).ravel()
+    rb = interior(b).ravel()
+    assert np.linalg.norm(rb - A @ xt) <= 1e-4 * np.linalg.norm(rb) * (1 + 1e-9)
+    assert np.linalg.norm(xt - x_np) > 1e-12 * np.linalg.norm(x_np)  # it is inexact
+
+
 # ------------------------------------------------------------------ eigenvalue estimate
 def test_lanczos_estimate_matches_numpy_and_bounds_the_spectrum():
     """eig_mode 1: the Lanczos estimate of the largest eigenvalue of D^-1 A
