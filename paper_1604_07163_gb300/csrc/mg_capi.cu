@@ -64,6 +64,7 @@ struct mg_handle {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int nsm = 152;
   int L = 0, lb = 0;  // levels; first level of the bottom kernel
+  int bot_cluster = 1;  // blocks of the bottom kernel (a cluster when > 1)
   LevelBuf lv[MG_MAX_LEVELS];
   double* Lc = nullptr;  // Cholesky factor of the coarsest operator
   double* Li = nullptr;  // its inverse and the transpose when the coarsest level has at most 32 unknowns
@@ -115,6 +116,26 @@ struct mg_handle {
 };
 
 namespace {
+
+// One thread-block cluster of nb blocks (a bottom kernel whose passes are
+// split over nb SMs).
+template <class... KArgs, class... Args>
+void launch_cluster(const mg_handle* h, void (*kern)(KArgs...), int nb, dim3 block, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = block;
+  cfg.stream = h->s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = h->prm.use_pdl ? 1 : 0;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = nb;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 template <class... KArgs, class... Args>
 void launch(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
@@ -279,6 +300,7 @@ void tm_collect(mg_handle* h) {
   if (!h->timing) return;
   for (const auto& r : h->pending) {
     float ms = 0.f;
+    cudaEventSynchronize(h->evpool[r.ev + 1]);  // launches queued after the last host sync may still run
     if (cudaEventElapsedTime(&ms, h->evpool[r.ev], h->evpool[r.ev + 1]) == cudaSuccess) {
       h->t_ms[r.cls][r.level] += ms;
       h->t_n[r.cls][r.level] += 1;
@@ -668,6 +690,24 @@ template <class TV, class TC> struct Impl {
     return cur;
   }
 
+  // whether a cluster of nb bottom-kernel blocks can be resident at once
+  static bool bottom_cluster_fits(int nb) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(BOT_THREADS);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = nb;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, k_bottom<TV, TV, TC, true>, &cfg) == cudaSuccess && n > 0;
+    cudaGetLastError();
+    return ok;
+  }
+
   static void bottom(mg_handle* h, int l0) {
     BotArgs<TV, TC> a{};
     a.nlev = h->L - l0;
@@ -698,7 +738,10 @@ template <class TV, class TC> struct Impl {
     a.coarse_maxit = h->prm.coarse_maxit;
     a.nc = h->nc;
     const int e = tm_begin(h, MG_K_BOTTOM, l0);
-    launch(h, k_bottom<TV, TV, TC>, dim3(1), dim3(BOT_THREADS), 0, a);
+    if (h->bot_cluster > 1)
+      launch_cluster(h, k_bottom<TV, TV, TC, true>, h->bot_cluster, dim3(BOT_THREADS), a);
+    else
+      launch(h, k_bottom<TV, TV, TC, false>, dim3(1), dim3(BOT_THREADS), 0, a);
     ++h->launches;
     tm_end(h, e, MG_K_BOTTOM, l0, (double)h->lv[l0].g.npts());
   }
@@ -994,6 +1037,15 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   // telescoping: first level whose unknowns fit the single-block bottom kernel
   h->lb = L - 1;
   while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
+  // a bottom kernel whose finest level has more than two points per thread
+  // of one block spreads over a cluster of up to 8 blocks (8 SMs)
+  {
+    const i64 n0 = h->lv[h->lb].g.npts();
+    int nb = 1;
+    while (nb < 8 && n0 > (i64)nb * BOT_THREADS * 2) nb *= 2;
+    if (nb > 1 && !dispatch(h, [&](auto impl) { return decltype(impl)::bottom_cluster_fits(nb); })) nb = 1;
+    h->bot_cluster = nb;
+  }
 
   const bool mixed = p.precision != MG_FP64;
   const size_t vb = vbytes(h), cb = cbytes(h);

@@ -63,16 +63,40 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(Op op, i64 n, double* pa
   }
 }
 
-// Single-block loop over all interior points of g (used inside the bottom
-// kernel).  The iteration space is padded to powers of two in x and y so the
-// point indices come from shifts and masks instead of divisions.
-template <class Op>
+// The bottom kernel runs as one thread block (CL = false) or as one
+// thread-block cluster (CL = true): the blocks of the cluster split every
+// pass, and a cluster barrier with release / acquire semantics separates the
+// passes.
+template <bool CL> struct BotSync {
+  static __device__ __forceinline__ unsigned rank() {
+    unsigned r = 0;
+    if constexpr (CL) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+  }
+  static __device__ __forceinline__ unsigned blocks() {
+    unsigned n = 1;
+    if constexpr (CL) asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+  }
+  static __device__ __forceinline__ void sync() {
+    if constexpr (CL)
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else __syncthreads();
+  }
+};
+
+// Loop of the bottom kernel's threads (of one block, or of all blocks of the
+// cluster) over all interior points of g.  The iteration space is padded to
+// powers of two in x and y so the point indices come from shifts and masks
+// instead of divisions.
+template <bool CL = false, class Op>
 __device__ __forceinline__ void block_for(const Op& op, const Geom& g) {
   const int lx = 32 - __clz(g.nx - 1), ly = 32 - __clz(g.ny - 1);  // ceil(log2)
   const unsigned n = (unsigned)g.nz << (lx + ly);
   const unsigned mx = (1u << lx) - 1, my = (1u << ly) - 1;
   double a0 = 0, a1 = 0;
-  for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
+  const unsigned t0 = BotSync<CL>::rank() * blockDim.x + threadIdx.x, step = BotSync<CL>::blocks() * blockDim.x;
+  for (unsigned t = t0; t < n; t += step) {
     const int i = (int)(t & mx), j = (int)((t >> lx) & my), k = (int)(t >> (lx + ly));
     if (i < g.nx && j < g.ny) op.template pt<false>(g, i, j, k, (int)g.at(i, j, k), a0, a1);
   }
@@ -467,26 +491,26 @@ template <class TV, class TC> struct BotArgs {
   int nc;
 };
 
-template <class R, class TV, class TC>
+template <class R, bool CL, class TV, class TC>
 __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const BotArgs<TV, TC>& a) {
   const R inv_theta = (R)L.inv_theta;
   int j0 = 0;
   if (zero) {
     if (a.degree == 1) {
       OpChebZero1<R, TV> op{L.b, L.dinv, L.x[cur ^ 1], inv_theta};
-      block_for(op, L.g);
-      __syncthreads();
+      block_for<CL>(op, L.g);
+      BotSync<CL>::sync();
       return cur ^ 1;
     }
     TV* dout = a.degree > 2 ? L.d : nullptr;
     if (L.w) {
       OpChebZero27<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], dout, L.w, L.g.len, (R)L.c1[1], (R)L.c2[1], inv_theta};
-      block_for(op, L.g);
+      block_for<CL>(op, L.g);
     } else {
       OpChebZero<R, TV, TC> op{L.b, L.dinv, L.x[cur ^ 1], dout, L.kx, L.ky, L.kz, (R)L.c1[1], (R)L.c2[1], inv_theta};
-      block_for(op, L.g);
+      block_for<CL>(op, L.g);
     }
-    __syncthreads();
+    BotSync<CL>::sync();
     cur ^= 1;
     j0 = 2;
   }
@@ -496,13 +520,13 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
     if (L.w) {
       OpChebStep27<R, TV, TC> op{L.x[cur], dprev, L.b, L.dinv, L.x[cur ^ 1], dout, L.w, L.g.len,
                                  (R)L.c1[j], (R)L.c2[j], inv_theta};
-      block_for(op, L.g);
+      block_for<CL>(op, L.g);
     } else {
       OpChebStep<R, TV, TC> op{L.x[cur], dprev, L.b, L.dinv, L.x[cur ^ 1], dout, L.kx, L.ky, L.kz,
                                (R)L.c1[j], (R)L.c2[j], inv_theta};
-      block_for(op, L.g);
+      block_for<CL>(op, L.g);
     }
-    __syncthreads();
+    BotSync<CL>::sync();
     cur ^= 1;
   }
   return cur;
@@ -649,68 +673,74 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
 }
 
 // L2 prefetch of n bytes at p, one 128-byte line per thread and step
-__device__ __forceinline__ void block_prefetch_l2(const void* p, i64 n) {
+// (threads number tid0 .. tid0 + nthreads - 1)
+__device__ __forceinline__ void block_prefetch_l2(const void* p, i64 n, unsigned tid0, unsigned nthreads) {
   if (!p) return;
-  for (i64 o = (i64)threadIdx.x * 128; o < n; o += (i64)blockDim.x * 128)
+  for (i64 o = (i64)tid0 * 128; o < n; o += (i64)nthreads * 128)
     asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)p + o));
 }
 
-template <class R, class TV, class TC>
+template <class R, class TV, class TC, bool CL>
 __global__ void __launch_bounds__(BOT_THREADS) k_bottom(const __grid_constant__ BotArgs<TV, TC> a) {
+  using BS = BotSync<CL>;
   pdl_wait();
   // The streaming passes on the fine levels evict these small arrays from L2
   // between V-cycles: request all of them at once instead of meeting the
   // misses one pass at a time.
+  const unsigned tid0 = BS::rank() * blockDim.x + threadIdx.x, nth = BS::blocks() * blockDim.x;
   for (int l = 0; l < a.nlev; ++l) {
     const BotLevel<TV, TC>& V = a.lv[l];
     const i64 nv = V.g.len * (i64)sizeof(TV), nc = V.g.len * (i64)sizeof(TC);
-    block_prefetch_l2(V.x[0], nv);
-    block_prefetch_l2(V.x[1], nv);
-    block_prefetch_l2(V.d, nv);
-    block_prefetch_l2(V.b, nv);
-    block_prefetch_l2(V.r, nv);
-    block_prefetch_l2(V.dinv, nv);
+    block_prefetch_l2(V.x[0], nv, tid0, nth);
+    block_prefetch_l2(V.x[1], nv, tid0, nth);
+    block_prefetch_l2(V.d, nv, tid0, nth);
+    block_prefetch_l2(V.b, nv, tid0, nth);
+    block_prefetch_l2(V.r, nv, tid0, nth);
+    block_prefetch_l2(V.dinv, nv, tid0, nth);
     if (V.w) {
-      block_prefetch_l2(V.w, 13 * nc);
-      block_prefetch_l2(V.dg, nv);
+      block_prefetch_l2(V.w, 13 * nc, tid0, nth);
+      block_prefetch_l2(V.dg, nv, tid0, nth);
     } else {
-      block_prefetch_l2(V.kx, nc);
-      block_prefetch_l2(V.ky, nc);
-      block_prefetch_l2(V.kz, nc);
+      block_prefetch_l2(V.kx, nc, tid0, nth);
+      block_prefetch_l2(V.ky, nc, tid0, nth);
+      block_prefetch_l2(V.kz, nc, tid0, nth);
     }
   }
-  if (a.Li) block_prefetch_l2(a.Li, 2 * (i64)a.nc * a.nc * (i64)sizeof(double));
+  if (a.Li) block_prefetch_l2(a.Li, 2 * (i64)a.nc * a.nc * (i64)sizeof(double), tid0, nth);
   int cur[BOT_MAX];
   const int L = a.nlev;
   for (int l = 0; l < L - 1; ++l) {
     const BotLevel<TV, TC>& V = a.lv[l];
     cur[l] = 0;
-    for (int s = 0; s < a.nu_pre; ++s) cur[l] = bot_sweep<R>(V, cur[l], s == 0, a);
+    for (int s = 0; s < a.nu_pre; ++s) cur[l] = bot_sweep<R, CL>(V, cur[l], s == 0, a);
     if (a.nu_pre == 0) {
-      for (i64 t = threadIdx.x; t < V.g.len; t += blockDim.x) V.x[0][t] = store_as<TV>(0.0);
-      __syncthreads();
+      for (i64 t = tid0; t < V.g.len; t += nth) V.x[0][t] = store_as<TV>(0.0);
+      BS::sync();
     }
     if (V.w) {
       OpResidual27<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.w, V.g.len, V.dg};
-      block_for(res, V.g);
+      block_for<CL>(res, V.g);
     } else {
       OpResidual<R, TV, TV, TC> res{V.x[cur[l]], V.b, V.r, V.kx, V.ky, V.kz};
-      block_for(res, V.g);
+      block_for<CL>(res, V.g);
     }
-    __syncthreads();
+    BS::sync();
     OpRestrict<R, TV> rs{V.g, V.r, a.lv[l + 1].b};
-    block_for(rs, a.lv[l + 1].g);
-    __syncthreads();
+    block_for<CL>(rs, a.lv[l + 1].g);
+    BS::sync();
   }
-  bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.Li, a.nc, a.Ac, a.coarse_rtol,
-                       a.coarse_maxit);
+  // the coarsest solve in the first block; its barriers are block-local
+  if (BS::rank() == 0)
+    bot_coarse_solve<TV>(a.lv[L - 1].g, a.lv[L - 1].b, a.lv[L - 1].x[0], a.Lc, a.Li, a.nc, a.Ac, a.coarse_rtol,
+                         a.coarse_maxit);
+  BS::sync();
   cur[L - 1] = 0;
   for (int l = L - 2; l >= 0; --l) {
     const BotLevel<TV, TC>& V = a.lv[l];
     OpProlong<R, TV> pr{a.lv[l + 1].g, a.lv[l + 1].x[cur[l + 1]], V.x[cur[l]]};
-    block_for(pr, V.g);
-    __syncthreads();
-    for (int s = 0; s < a.nu_post; ++s) cur[l] = bot_sweep<R>(V, cur[l], false, a);
+    block_for<CL>(pr, V.g);
+    BS::sync();
+    for (int s = 0; s < a.nu_post; ++s) cur[l] = bot_sweep<R, CL>(V, cur[l], false, a);
   }
 }
 
