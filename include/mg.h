@@ -130,6 +130,9 @@ typedef struct {
                           1 needs a coarsest level of at most 32 unknowns */
   double coarse_rtol;  /* relative residual of the inexact coarse solve (default 1e-4) */
   int coarse_maxit;    /* its iteration limit, 1..32 (default 30) */
+  int bottom_blocks;   /* blocks of the bottom kernel: 0 (default) chosen from the size of its finest
+                          level; 1 one block; 2, 4 or 8 one thread-block cluster that splits every pass.
+                          The result is bitwise the same for every choice */
 } mg_params;
 
 typedef struct {

@@ -35,6 +35,7 @@ class MgParams(C.Structure):
         ("smoother", C.c_int), ("richardson_omega", C.c_double), ("coarse_op", C.c_int),
         ("krylov", C.c_int), ("gmres_restart", C.c_int), ("eig_mode", C.c_int), ("eig_safety", C.c_double),
         ("coarse_solve", C.c_int), ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int),
+        ("bottom_blocks", C.c_int),
     ]
 
 

@@ -67,7 +67,7 @@ struct mg_handle {
   int bot_cluster = 1;  // blocks of the bottom kernel (a cluster when > 1)
   LevelBuf lv[MG_MAX_LEVELS];
   double* Lc = nullptr;  // Cholesky factor of the coarsest operator
-  double* Li = nullptr;  // its inverse and the transpose when the coarsest level has at most 32 unknowns
+  double* Li = nullptr;  // L^-1 and the coarsest operator inverse when that level has at most 32 unknowns
   double* Ac = nullptr;  // the dense coarsest operator (inexact coarse solve)
   // flexible GMRES: basis V_0..V_m (float64), preconditioned Z_0..Z_{m-1}
   // (V-cycle precision), one column's dots and the coefficients y, partial sums
@@ -726,7 +726,13 @@ template <class TV, class TC> struct Impl {
       B.kz = C(Lv.kz);
       B.w = Lv.g27 ? C(Lv.w) : nullptr;
       B.dg = Lv.g27 ? V(Lv.dg) : nullptr;
-      cheb_table(h->prm, Lv.beta, Lv.alpha, &B.inv_theta, B.c1, B.c2);
+      double it, c1[BOT_MAXDEG], c2[BOT_MAXDEG];
+      cheb_table(h->prm, Lv.beta, Lv.alpha, &it, c1, c2);
+      B.inv_theta = (TV)it;
+      for (int j = 0; j < h->prm.cheby_degree; ++j) {
+        B.c1[j] = (TV)c1[j];
+        B.c2[j] = (TV)c2[j];
+      }
     }
     a.nu_pre = h->prm.nu_pre;
     a.nu_post = h->prm.nu_post;
@@ -1037,12 +1043,17 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   // telescoping: first level whose unknowns fit the single-block bottom kernel
   h->lb = L - 1;
   while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
-  // a bottom kernel whose finest level has more than two points per thread
-  // of one block spreads over a cluster of up to 8 blocks (8 SMs)
+  // In float64 the bottom kernel's passes are bound by the float64 pipe of
+  // its SM: a finest bottom level of more than one point per thread spreads
+  // over a cluster of up to 8 blocks (8 SMs).  The float32 passes are bound
+  // by latency and barriers, which a cluster barrier does not improve
+  // (measured on GB300: one block is as fast as 4 or 8, faster than 2).
   {
     const i64 n0 = h->lv[h->lb].g.npts();
     int nb = 1;
-    while (nb < 8 && n0 > (i64)nb * BOT_THREADS * 2) nb *= 2;
+    if (p.precision == MG_FP64)
+      while (nb < 8 && n0 > (i64)nb * BOT_THREADS) nb *= 2;
+    if (p.bottom_blocks > 0) nb = p.bottom_blocks;
     if (nb > 1 && !dispatch(h, [&](auto impl) { return decltype(impl)::bottom_cluster_fits(nb); })) nb = 1;
     h->bot_cluster = nb;
   }
@@ -1627,6 +1638,7 @@ mg_status mg_params_default(mg_params* p) {
   p->coarse_solve = 0;
   p->coarse_rtol = 1e-4;
   p->coarse_maxit = 30;
+  p->bottom_blocks = 0;
   return MG_OK;
 }
 
@@ -1647,7 +1659,7 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN || p.krylov < MG_KRYLOV_CG ||
       p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256 || p.eig_mode < 0 ||
       p.eig_mode > 1 || !(p.eig_safety > 0.0) || p.coarse_solve < 0 || p.coarse_solve > 1 ||
-      !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32)
+      !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32 || (p.bottom_blocks != 0 && p.bottom_blocks != 1 && p.bottom_blocks != 2 && p.bottom_blocks != 4 && p.bottom_blocks != 8))
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible

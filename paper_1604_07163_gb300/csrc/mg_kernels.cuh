@@ -289,24 +289,32 @@ __global__ void k_cholesky(double* A, int n, int* bad) {
     if (t % n > t / n) A[t] = 0.0;
 }
 
-// Inverse of the lower-triangular Cholesky factor L (n <= 32), row-major,
-// for the coarse solve's two triangular products: Li[0, n*n) holds L^-1 and
-// Li[n*n, 2*n*n) its transpose.  Thread c solves L v = e_c by forward
-// substitution (column c of L^-1).
+// Coarsest operator inverse from its Cholesky factor L (n <= 32), row-major,
+// for a coarse solve that is one matrix-vector product: Li[0, n*n) receives
+// L^-1 (thread c solves L v = e_c by forward substitution, column c) and
+// Li[n*n, 2*n*n) the symmetric A^-1 = L^-T L^-1 (entry (l, c) sums
+// L^-1(m, l) L^-1(m, c) over m >= max(l, c) in increasing m, so (l, c) and
+// (c, l) are the same sum).
 __global__ void k_trinv(const double* L, double* Li, int n) {
   const int c = threadIdx.x;
-  if (c >= n) return;
-  double* LiT = Li + (i64)n * n;
-  for (int r = 0; r < n; ++r) {
-    double v = 0.0;
-    if (r >= c) {
-      double s = r == c ? 1.0 : 0.0;
-      for (int q = c; q < r; ++q) s -= L[(i64)r * n + q] * Li[(i64)q * n + c];
-      v = s / L[(i64)r * n + r];
+  double* Ai = Li + (i64)n * n;
+  if (c < n)
+    for (int r = 0; r < n; ++r) {
+      double v = 0.0;
+      if (r >= c) {
+        double s = r == c ? 1.0 : 0.0;
+        for (int q = c; q < r; ++q) s -= L[(i64)r * n + q] * Li[(i64)q * n + c];
+        v = s / L[(i64)r * n + r];
+      }
+      Li[(i64)r * n + c] = v;
     }
-    Li[(i64)r * n + c] = v;
-    LiT[(i64)c * n + r] = v;
-  }
+  __syncthreads();
+  if (c < n)
+    for (int l = 0; l < n; ++l) {
+      double s = 0.0;
+      for (int m = l > c ? l : c; m < n; ++m) s = fma(Li[(i64)m * n + l], Li[(i64)m * n + c], s);
+      Ai[(i64)l * n + c] = s;
+    }
 }
 
 // ------------------------------------------------------------ eigenvalue estimate
@@ -475,8 +483,11 @@ template <class TV, class TC> struct BotLevel {
   const TC *kx, *ky, *kz;
   const TC* w;    // Galerkin level: 13 coupling arrays of length g.len (else null)
   const TV* dg;   // and its diagonal
-  double inv_theta;                       // Chebyshev step j = 0: d_0 = s_0 / theta
-  double c1[BOT_MAXDEG], c2[BOT_MAXDEG];  // step j >= 1: d_j = c1[j] d_{j-1} + c2[j] s_j
+  // Chebyshev constants, rounded to the vector type on the host: a float64
+  // to float32 conversion per thread and pass would run on GB300's scarce
+  // float64 pipe and dominate the passes of the float32 bottom kernel.
+  TV inv_theta;                       // step j = 0: d_0 = s_0 / theta
+  TV c1[BOT_MAXDEG], c2[BOT_MAXDEG];  // step j >= 1: d_j = c1[j] d_{j-1} + c2[j] s_j
 };
 
 template <class TV, class TC> struct BotArgs {
@@ -484,7 +495,7 @@ template <class TV, class TC> struct BotArgs {
   int nlev;            // levels in this kernel; the last one is the coarsest
   int nu_pre, nu_post, degree;
   const double* Lc;    // Cholesky factor of the coarsest operator (n x n)
-  const double* Li;    // its inverse, then the transpose (n <= 32), else null
+  const double* Li;    // L^-1, then the operator inverse L^-T L^-1 (n <= 32), else null
   const double* Ac;    // the coarsest operator itself (inexact solve), else null
   double coarse_rtol;  // inexact solve: GMRES-Jacobi to this relative residual,
   int coarse_maxit;    // at most this many steps (<= 32)
@@ -624,7 +635,7 @@ template <class TV>
 __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double* Lc, const double* Li, int n,
                                  const double* Ac = nullptr, double crtol = 0.0, int cmaxit = 0) {
   __shared__ double y[1024];
-  __shared__ double t[32];
+  __shared__ double part[8 * 32];
   for (int u = threadIdx.x; u < n; u += blockDim.x) {
     const int i = u % g.nx, j = (u / g.nx) % g.ny, k = u / (g.nx * g.ny);
     y[u] = cvt<double>(b[g.at(i, j, k)]);
@@ -633,22 +644,28 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
   if (Ac && n <= 32) {
     if (threadIdx.x < 32) warp_gmres(Ac, n, crtol, cmaxit, y);
   } else if (n <= 32 && Li) {
-    // one warp: lane w forms row w of each product with n multiply-adds (the
-    // float64 pipe issues per warp instruction, so one warp of n steps costs
-    // less than n warps of shuffle-tree sums)
-    if (threadIdx.x < 32) {
-      const int w = threadIdx.x;
-      double v = 0.0;
-      const double* LiT = Li + n * n;
-      for (int l = 0; l < n; ++l)  // t = L^-1 y (lanes read consecutive entries of the transpose)
-        if (w < n && l <= w) v = fma(LiT[l * n + w], y[l], v);
-      if (w < n) t[w] = v;
-      __syncwarp();
-      v = 0.0;
-      for (int l = 0; l < n; ++l)  // y = L^-T t
-        if (w < n && l >= w) v = fma(Li[l * n + w], t[l], v);
-      __syncwarp();
-      if (w < n) y[w] = v;
+    // y = A^-1 y with the precomputed symmetric inverse: warp q < 8 sums
+    // columns q, q + 8, q + 16, q + 24 (lane w forms row w; its at most four
+    // matrix entries are loaded before the first multiply-add, so the
+    // chain is one load latency and four float64 FMAs), then thread w adds
+    // the eight partial rows in warp order.
+    const double* Ai = Li + n * n;
+    const int w = threadIdx.x & 31, q = threadIdx.x >> 5;
+    double v = 0.0;
+    if (q < 8 && w < n) {
+      double e[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) e[s] = q + 8 * s < n ? Ai[(q + 8 * s) * n + w] : 0.0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (q + 8 * s < n) v = fma(e[s], y[q + 8 * s], v);
+    }
+    if (q < 8) part[q * 32 + w] = v;
+    __syncthreads();
+    if (threadIdx.x < n) {
+      double r = part[threadIdx.x];
+      for (int u = 1; u < 8; ++u) r += part[u * 32 + threadIdx.x];
+      y[threadIdx.x] = r;
     }
   } else {
     for (int c = 0; c < n; ++c) {

@@ -43,6 +43,7 @@ class Params:
     coarse_solve: str = "cholesky"  # or "gmres" (Jacobi-preconditioned, to coarse_rtol; use krylov="fgmres")
     coarse_rtol: float = 1e-4
     coarse_maxit: int = 30
+    bottom_blocks: int = 0  # 0 automatic; 1 one block; 2, 4, 8 a thread-block cluster
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -60,6 +61,7 @@ class Params:
         p.coarse_solve = {"cholesky": 0, "gmres": 1}[self.coarse_solve]
         p.coarse_rtol = self.coarse_rtol
         p.coarse_maxit = self.coarse_maxit
+        p.bottom_blocks = self.bottom_blocks
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p

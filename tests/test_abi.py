@@ -52,7 +52,8 @@ def test_params_struct_layout_and_defaults(lib):
     assert p.precision == 0 and p.face_rule == 0 and p.coarse_k_rule == 0 and p.flexible == -1
     assert (p.stencil_kernel, p.use_pdl, p.smoother, p.richardson_omega, p.coarse_op, p.krylov,
             p.gmres_restart, p.eig_mode, p.eig_safety,
-            p.coarse_solve, p.coarse_rtol, p.coarse_maxit) == (0, 1, 0, 6.0 / 7.0, 0, 0, 30, 0, 1.1, 0, 1e-4, 30)
+            p.coarse_solve, p.coarse_rtol, p.coarse_maxit, p.bottom_blocks) == (
+                0, 1, 0, 6.0 / 7.0, 0, 0, 30, 0, 1.1, 0, 1e-4, 30, 0)
     assert lib.mg_params_default(None) == 1
 
 
@@ -85,6 +86,10 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
     lib.mg_params_default(ctypes.byref(p))
     for mode, rtol, maxit in ((2, 1e-4, 30), (1, 0.0, 30), (1, 1e-4, 0), (1, 1e-4, 33)):
         p.coarse_solve, p.coarse_rtol, p.coarse_maxit = mode, rtol, maxit
+        assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
+    lib.mg_params_default(ctypes.byref(p))
+    for blocks in (3, 16, -1):
+        p.bottom_blocks = blocks
         assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
     assert lib.mg_free(None) == 0
     assert lib.mg_num_levels(None) == 0

@@ -305,6 +305,26 @@ def test_telescoping_graph_and_kernel_choice_do_not_change_the_result(gpu_lib):
             assert rel2(N(x), ref[0]) < 1e-13
 
 
+def test_bottom_kernel_block_count_leaves_the_result_unchanged(gpu_lib):
+    """The bottom kernel (levels 15^3, 7^3, 3^3 and the coarsest solve here)
+    runs as one block or as a thread-block cluster of 2, 4 or 8 blocks that
+    split every pass between cluster barriers.  Each point is computed by the
+    same arithmetic whichever block owns it, so every precision and coarse
+    operator gives the same iterates bit for bit for every block count."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64", 65)
+    for prec in ("fp64", "mixed_fp32", "mixed_bf16k"):
+        for cop in ("rediscretised", "galerkin"):
+            out = []
+            for nb in (0, 1, 2, 4, 8):
+                x, st = mg.MGSolver(T(k), mg.Params(precision=prec, coarse_op=cop, bottom_blocks=nb)).solve(
+                    T(f), 1e-10)
+                out.append((x, st.iters, st.rel_resid))
+            for o in out[1:]:
+                assert o[1] == out[0][1] and o[2] == out[0][2]
+                assert torch.equal(o[0], out[0][0]), (prec, cop)
+
+
 def test_repeated_solves_bitwise_identical(gpu_lib):
     import paper_1604_07163_gb300 as mg
     dims, k, f, spec = mi.workload("poisson33_fp64", 65)
