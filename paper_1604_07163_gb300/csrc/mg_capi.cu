@@ -642,6 +642,13 @@ template <class TV, class TC> struct Impl {
       zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
       return cur ^ 1;
     }
+    if constexpr (std::is_same<TV, double>::value) {
+      if (!Lv.zs && !Lv.tma) {  // store step 0, then step 1 as an ordinary step (OpChebStart)
+        OpChebStart<TV, TV> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur]), V(Lv.d), inv_theta};
+        zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
+        return cheb_steps(h, l, cur, 1, 1.0 / sigma, fuse_rz);
+      }
+    }
     const double rho_prev = 1.0 / sigma;
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
     const double c1 = rho * rho_prev, c2 = 2.0 * rho / delta;

@@ -267,6 +267,27 @@ template <class R, class TV> struct OpChebZero1 {
   }
 };
 
+// Chebyshev step 0 from a zero guess stored as both iterate and direction,
+// x = d = D^-1 b / theta (the value LdJac forms), so that step 1 runs as an
+// ordinary step.  The float64 forms use it: forming D^-1 b / theta again at
+// every neighbour of every point, as the fused zero-guess step does, costs
+// two float64 multiplications per neighbour on GB300's slow float64 pipe.
+// Step 1 from the stored values gives the fused step's result bit for bit.
+template <class R, class TV> struct OpChebStart {
+  using Real = R;
+  const TV* b;
+  const TV* dinv;
+  TV* x;
+  TV* d;
+  R inv_theta;
+  __device__ void prepare() {}
+  template <bool NC> __device__ __forceinline__ void pt(const Geom&, int, int, int, int p, double&, double&) const {
+    const TV v = store_as<TV>(inv_theta * (cvt<R>(ldp<NC>(dinv + p)) * cvt<R>(ldp<NC>(b + p))));
+    x[p] = v;
+    d[p] = v;
+  }
+};
+
 // r = b - A x
 template <class R, class TV, class TB, class TC> struct OpResidual {
   using Real = R;

@@ -506,6 +506,13 @@ template <class R, bool CL, class TV, class TC>
 __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const BotArgs<TV, TC>& a) {
   const R inv_theta = (R)L.inv_theta;
   int j0 = 0;
+  if (zero && sizeof(R) == 8 && a.degree > 1) {  // float64: store step 0, then step 1 as an ordinary step
+    OpChebStart<R, TV> op{L.b, L.dinv, L.x[cur], L.d, inv_theta};
+    block_for<CL>(op, L.g);
+    BotSync<CL>::sync();
+    zero = false;
+    j0 = 1;
+  }
   if (zero) {
     if (a.degree == 1) {
       OpChebZero1<R, TV> op{L.b, L.dinv, L.x[cur ^ 1], inv_theta};
