@@ -417,15 +417,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 453.0 MB; step 1 with r.z: 604.9 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (529.0e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (399.5e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (395.5e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (83.1e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (68.2e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (792.0e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (550.8e6, "e4852069271570e4"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (416.7e6, "e4852069271570e4"),
+    # 453.0 MB; step 1 with r.z: 604.8 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (528.9e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (399.4e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (395.4e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (82.9e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (68.4e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (792.5e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (551.0e6, "50bcb3737d943545"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (416.7e6, "50bcb3737d943545"),
 }
 
 
