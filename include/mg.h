@@ -96,9 +96,10 @@ typedef struct {
   int maxit;           /* CG iteration limit (default 1000) */
   int nonzero_guess;   /* 1: mg_solve starts from the x passed in */
   int flexible;        /* CG beta: 0 Fletcher-Reeves, 1 Polak-Ribiere (flexible); -1 (default) = 0 */
-  int telescope_max_n; /* levels with at most this many unknowns run inside one thread block (default 4096) */
+  int telescope_max_n; /* levels with at most this many unknowns run inside the bottom kernel, one thread block
+                          or one thread-block cluster (bottom_blocks) (default 4096) */
   int use_graph;       /* 1: replay the V-cycle from a captured CUDA graph (default 1) */
-  int stencil_kernel;  /* smoother/residual kernels on the levels above the single-block bottom:
+  int stencil_kernel;  /* smoother/residual kernels on the levels above the bottom kernel:
                           0 (default) z-marching, 64x4 tiles of two consecutive points per
                             thread: vector loads, x neighbours by warp shuffles, z neighbours
                             in registers, L2 prefetch two planes ahead (the fastest measured
@@ -258,7 +259,7 @@ typedef enum {
   MG_K_RESID = 2,      /* r = b - A x */
   MG_K_RESTRICT = 3,   /* full weighting (points = coarse points) */
   MG_K_PROLONG = 4,    /* x += P e */
-  MG_K_BOTTOM = 5,     /* telescoped single-block levels + coarse Cholesky solve */
+  MG_K_BOTTOM = 5,     /* telescoped bottom levels + coarsest solve, one block or one cluster */
   MG_K_CG_DIR = 6,     /* p = z + beta p (float64) */
   MG_K_CG_UPD = 7,     /* x += alpha p, r -= alpha q, r.r (float64) */
   MG_K_DOT = 8,        /* r.z (float64 accumulation) */

@@ -1047,7 +1047,7 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   const Geom& gc = h->lv[L - 1].g;
   h->nc = (int)gc.npts();
   if (h->nc > MG_MAX_COARSE) return fail(h, MG_ERR_ARG, "coarsest level exceeds MG_MAX_COARSE unknowns");
-  // telescoping: first level whose unknowns fit the single-block bottom kernel
+  // telescoping: first level whose unknowns fit the bottom kernel
   h->lb = L - 1;
   while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
   // In float64 the bottom kernel's passes are bound by the float64 pipe of

@@ -122,8 +122,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16>(flo
 }
 
 // Loads: NC = true uses the read-only path (data not written by this kernel);
-// NC = false is a plain coherent load (the single-block bottom kernel reads
-// what its own threads wrote before a __syncthreads()).
+// NC = false is a plain coherent load (the bottom kernel reads what its own
+// threads, or its cluster's, wrote before a barrier).
 template <bool NC, class T> __device__ __forceinline__ T ldp(const T* p) {
   if constexpr (NC) return __ldg(p);
   else return *p;

@@ -551,8 +551,8 @@ __device__ int bot_sweep(const BotLevel<TV, TC>& L, int cur, bool zero, const Bo
 }
 
 // Coarsest solve x = L^-T L^-1 b in float64 with the Cholesky factor.  For
-// n <= 32 the two triangular solves are products with the precomputed L^-1:
-// a substitution is a chain of n dependent divisions and shuffles, slow on
+// n <= 32 it is one product with the precomputed inverse (k_trinv): a
+// substitution is a chain of n dependent divisions and shuffles, slow on
 // GB300's float64 pipe.  Larger n substitute with the whole block.
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll

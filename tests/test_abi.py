@@ -93,3 +93,14 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
         assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
     assert lib.mg_free(None) == 0
     assert lib.mg_num_levels(None) == 0
+
+
+def test_source_hash_ignores_comments_only():
+    """bench.csrc_hash keys the ncu traffic table: editing a comment or the
+    layout of a kernel source leaves it unchanged, editing code changes it."""
+    import bench
+    base = {"k.cu": "// a kernel\n__global__ void k(float* x) { x[0] = 1.0f; /* store */ }\n"}
+    comment = {"k.cu": "// the kernel, reworded\n__global__  void k(float* x)\n{ x[0] = 1.0f; }\n"}
+    code = {"k.cu": "// a kernel\n__global__ void k(float* x) { x[0] = 2.0f; /* store */ }\n"}
+    assert bench.csrc_hash(base) == bench.csrc_hash(comment)
+    assert bench.csrc_hash(base) != bench.csrc_hash(code)
