@@ -381,7 +381,9 @@ def run_ours(args):
     if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.adjoint
             and args.coarse_op == "rediscretised"):
         its = forms.get("fp64", forms[HEADLINE])["iters"]
-        sample = 20
+        # about 12 s of PCG iterations on the 16 host cores of a GB300 machine
+        # (0.15 s per iteration there), never more than the solve takes
+        sample = min(80, its)
         v, dt, cores = oracle_sample(spec, its, sample)
         cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
                "sample": f"{sample} PCG iterations of the CPU FP64 oracle on the full {spec['N']}^3 workload "
