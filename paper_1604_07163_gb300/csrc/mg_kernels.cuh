@@ -563,65 +563,90 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // Inexact coarsest solve (the truncated coarse solve of the paper's Sec. 5):
 // GMRES with the Jacobi preconditioner on the right, classical Gram-Schmidt,
 // Givens rotations, from zero, stopped when the rotated residual norm is at
-// most rtol ||b|| or after m (<= 32) steps.  One warp, lane i holding
-// component i (n <= 32); the Krylov basis and the Hessenberg columns live in
-// shared memory; lane 0 applies the rotations.  y holds b on entry and x on
-// exit.
-__device__ void warp_gmres(const double* A, int n, double rtol, int m, double* y) {
-  __shared__ double Vs[33 * 32], Hs[33 * 32], gs[33], cs[32], sn[32], ys[32];
-  __shared__ int jj_s;
-  const int lane = threadIdx.x;
+// most rtol ||b|| or after m (<= 32) steps.  Called by all threads of one
+// block of at least 32 warps; lane i of a warp holds component i (n <= 32);
+// the Krylov basis and the Hessenberg columns live in shared memory.  Per
+// step: warps 0-7 form the matrix-vector product from column groups (their
+// partial rows added in warp order), warp i forms the Gram-Schmidt
+// coefficient of basis vector i (all from the same w), and warp 0 updates w,
+// normalises it and (lane 0) applies the rotations.  y holds b on entry and
+// x on exit.
+__device__ void block_gmres(const double* A, int n, double rtol, int m, double* y) {
+  __shared__ double Vs[33 * 32], Hs[33 * 32], gs[33], cs[32], sn[32], ys[32], zs[32], ws[32], part[8 * 32];
+  __shared__ double beta_s;
+  __shared__ int jj_s, stop_s;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const bool on = lane < n;
-  const double bi = on ? y[lane] : 0.0;
   const double dl = on ? A[lane * n + lane] : 1.0;
-  const double beta = sqrt(warp_sum_d(bi * bi));
-  double xo = 0.0;
-  if (beta > 0.0) {
-    Vs[lane] = bi / beta;
+  if (wq == 0) {
+    const double bi = on ? y[lane] : 0.0;
+    const double beta = sqrt(warp_sum_d(bi * bi));
     if (lane == 0) {
+      beta_s = beta;
       for (int i = 0; i <= m; ++i) gs[i] = 0.0;
       gs[0] = beta;
       jj_s = 0;
+      stop_s = 0;
     }
-    __syncwarp();
+    if (beta > 0.0) Vs[lane] = bi / beta;
+  }
+  __syncthreads();
+  const double beta = beta_s;
+  if (beta > 0.0) {
     for (int j = 0; j < m; ++j) {
-      const double z = on ? Vs[j * 32 + lane] / dl : 0.0;
-      double w = 0.0;
-      for (int k = 0; k < n; ++k) {
-        const double zk = __shfl_sync(0xffffffffu, z, k);
-        if (on) w = fma(A[lane * n + k], zk, w);
-      }
-      for (int i = 0; i <= j; ++i) {  // all coefficients from the same w
-        const double h = warp_sum_d(w * Vs[i * 32 + lane]);
-        if (lane == 0) Hs[i * 32 + j] = h;
-      }
-      __syncwarp();
-      for (int i = 0; i <= j; ++i) w -= Hs[i * 32 + j] * Vs[i * 32 + lane];
-      const double hn = sqrt(warp_sum_d(w * w));
-      if (hn > 0.0) Vs[(j + 1) * 32 + lane] = w / hn;
-      if (lane == 0) {
-        Hs[(j + 1) * 32 + j] = hn;
-        for (int i = 0; i < j; ++i) {
-          const double a = Hs[i * 32 + j], c = Hs[(i + 1) * 32 + j];
-          Hs[i * 32 + j] = cs[i] * a + sn[i] * c;
-          Hs[(i + 1) * 32 + j] = -sn[i] * a + cs[i] * c;
+      if (wq == 0) zs[lane] = on ? Vs[j * 32 + lane] / dl : 0.0;
+      __syncthreads();
+      if (wq < 8) {  // w = A z: warp q sums columns q, q + 8, q + 16, q + 24
+        double v = 0.0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int k = wq + 8 * s;
+          if (on && k < n) v = fma(A[lane * n + k], zs[k], v);
         }
-        const double a = Hs[j * 32 + j], c = Hs[(j + 1) * 32 + j];
-        const double d = sqrt(a * a + c * c);
-        if (d > 0.0) {
-          cs[j] = a / d;
-          sn[j] = c / d;
-          Hs[j * 32 + j] = d;
-          Hs[(j + 1) * 32 + j] = 0.0;
-          gs[j + 1] = -sn[j] * gs[j];
-          gs[j] = cs[j] * gs[j];
-          jj_s = j + 1;
+        part[wq * 32 + lane] = v;
+      }
+      __syncthreads();
+      if (wq == 0) {
+        double w = part[lane];
+        for (int q = 1; q < 8; ++q) w += part[q * 32 + lane];
+        ws[lane] = on ? w : 0.0;
+      }
+      __syncthreads();
+      if (wq <= j) {  // all coefficients from the same w
+        const double h = warp_sum_d(ws[lane] * Vs[wq * 32 + lane]);
+        if (lane == 0) Hs[wq * 32 + j] = h;
+      }
+      __syncthreads();
+      if (wq == 0) {
+        double w = ws[lane];
+        for (int i = 0; i <= j; ++i) w -= Hs[i * 32 + j] * Vs[i * 32 + lane];
+        const double hn = sqrt(warp_sum_d(w * w));
+        if (hn > 0.0) Vs[(j + 1) * 32 + lane] = w / hn;
+        if (lane == 0) {
+          Hs[(j + 1) * 32 + j] = hn;
+          for (int i = 0; i < j; ++i) {
+            const double a = Hs[i * 32 + j], c = Hs[(i + 1) * 32 + j];
+            Hs[i * 32 + j] = cs[i] * a + sn[i] * c;
+            Hs[(i + 1) * 32 + j] = -sn[i] * a + cs[i] * c;
+          }
+          const double a = Hs[j * 32 + j], c = Hs[(j + 1) * 32 + j];
+          const double d = sqrt(a * a + c * c);
+          if (d > 0.0) {
+            cs[j] = a / d;
+            sn[j] = c / d;
+            Hs[j * 32 + j] = d;
+            Hs[(j + 1) * 32 + j] = 0.0;
+            gs[j + 1] = -sn[j] * gs[j];
+            gs[j] = cs[j] * gs[j];
+            jj_s = j + 1;
+          }
+          stop_s = jj_s != j + 1 || fabs(gs[j + 1]) <= rtol * beta || hn == 0.0;
         }
       }
-      __syncwarp();
-      if (jj_s != j + 1 || fabs(gs[j + 1]) <= rtol * beta || hn == 0.0) break;
+      __syncthreads();
+      if (stop_s) break;
     }
-    if (lane == 0) {  // R y = g
+    if (threadIdx.x == 0) {  // R y = g
       const int jj = jj_s;
       for (int i = jj - 1; i >= 0; --i) {
         double v = gs[i];
@@ -629,13 +654,18 @@ __device__ void warp_gmres(const double* A, int n, double rtol, int m, double* y
         ys[i] = v / Hs[i * 32 + i];
       }
     }
-    __syncwarp();
-    double sacc = 0.0;
-    for (int k = 0; k < jj_s; ++k) sacc += ys[k] * Vs[k * 32 + lane];
-    xo = sacc / dl;
+    __syncthreads();
   }
-  if (on) y[lane] = xo;
-  __syncwarp();
+  if (wq == 0) {
+    double xo = 0.0;
+    if (beta > 0.0) {
+      double sacc = 0.0;
+      for (int k = 0; k < jj_s; ++k) sacc += ys[k] * Vs[k * 32 + lane];
+      xo = sacc / dl;
+    }
+    if (on) y[lane] = xo;
+  }
+  __syncthreads();
 }
 
 template <class TV>
@@ -649,7 +679,7 @@ __device__ void bot_coarse_solve(const Geom& g, const TV* b, TV* x, const double
   }
   __syncthreads();
   if (Ac && n <= 32) {
-    if (threadIdx.x < 32) warp_gmres(Ac, n, crtol, cmaxit, y);
+    block_gmres(Ac, n, crtol, cmaxit, y);
   } else if (n <= 32 && Li) {
     // y = A^-1 y with the precomputed symmetric inverse: warp q < 8 sums
     // columns q, q + 8, q + 16, q + 24 (lane w forms row w; its at most four
