@@ -419,15 +419,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 453.0 MB; step 1 with r.z: 604.8 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (528.9e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (399.4e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (395.4e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (82.9e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (68.4e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (792.5e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (551.0e6, "696a4f14ec5dbab0"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (416.7e6, "696a4f14ec5dbab0"),
+    # 452.8 MB; step 1 with r.z: 604.5 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (528.7e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (399.6e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (395.9e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (82.4e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (68.6e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (792.1e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (551.3e6, "43150c3603489433"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (416.9e6, "43150c3603489433"),
 }
 
 
