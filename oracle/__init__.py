@@ -84,6 +84,10 @@ def _load():
         lib.orc_fgmres.argtypes = [vp, _dptr, _dptr, C.c_double, C.c_int, C.c_int, vp, _dptr]
         lib.orc_set_smoother.restype = C.c_int
         lib.orc_set_smoother.argtypes = [vp, C.c_int, C.c_double]
+        lib.orc_set_sum_order.restype = C.c_int
+        lib.orc_set_sum_order.argtypes = [vp, C.c_int]
+        lib.orc_dot.restype = C.c_double
+        lib.orc_dot.argtypes = [vp, C.c_long, _dptr, _dptr]
         _lib = lib
     return _lib
 
@@ -105,13 +109,16 @@ class Oracle:
                  degree: int = 2, eig_lo_frac: float = 0.1, eig_hi: float = 2.0,
                  coarse_rule: int = 0, face_rule: int = 0, smoother: int = 0, omega: float = 6.0 / 7.0,
                  galerkin: bool = False, eig_mode: int = 0, eig_safety: float = 1.1, coarse_gmres: bool = False,
-                 coarse_rtol: float = 1e-4, coarse_maxit: int = 30):
+                 coarse_rtol: float = 1e-4, coarse_maxit: int = 30, sum_order: int = 0):
         """smoother 0: Chebyshev(degree)-Jacobi sweeps; 1: Richardson-Jacobi
         iterations x += omega D^-1 (b - A x), nu_pre / nu_post of them.
         galerkin: coarse operators R A P instead of re-discretisation.
         eig_mode 1: per-level Chebyshev interval [eig_lo_frac L, eig_safety L]
         from a 10-step Lanczos estimate L of the largest eigenvalue of D^-1 A.
-        coarse_gmres: inexact coarsest solve, GMRES with Jacobi to coarse_rtol."""
+        coarse_gmres: inexact coarsest solve, GMRES with Jacobi to coarse_rtol.
+        sum_order 1: the second fixed summation order (pairwise dot products,
+        operator rows summed in decreasing column order), for measuring how
+        much rounding order alone moves a solve."""
         lib = _load()
         k = np.ascontiguousarray(k_cells, dtype=np.float64)
         self.dims = tuple(s + 1 for s in k.shape)
@@ -128,6 +135,8 @@ class Oracle:
             raise ValueError("oracle: invalid eigenvalue-estimate mode")
         if coarse_gmres and lib.orc_set_coarse(self._h, 1, coarse_rtol, coarse_maxit) != 0:
             raise ValueError("oracle: invalid coarse-solve settings")
+        if sum_order and lib.orc_set_sum_order(self._h, sum_order) != 0:
+            raise ValueError("oracle: invalid summation order")
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -145,6 +154,12 @@ class Oracle:
     def level_lanczos(self, l: int) -> float:
         """Lanczos estimate of the largest eigenvalue of D^-1 A on level l."""
         return self._lib.orc_level_lanczos(self._h, l)
+
+    def dot(self, a, b) -> float:
+        """a . b (flattened) in this hierarchy's summation order."""
+        a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+        b = np.ascontiguousarray(b, dtype=np.float64).ravel()
+        return self._lib.orc_dot(self._h, a.size, a, b)
 
     def level_dims(self, l: int):
         N = (C.c_int * 3)()

@@ -56,6 +56,9 @@ typedef struct {
   double *b, *x, *r, *s, *d, *t; /* work vectors (interior numbering) */
   int face_rule;
   double alpha, beta;  /* Chebyshev interval for D^-1 A on this level */
+  int sum_order;       /* 0: every sum in index order; 1: the second fixed order
+                          (pairwise dot products, CSR rows summed from the last
+                          stored entry to the first) */
 } olevel;
 
 typedef struct {
@@ -193,7 +196,18 @@ static int assemble(olevel *L) {
   return 0;
 }
 
+/* y = A x.  Each row is summed in increasing column order, or (second
+ * summation order) in decreasing column order. */
 static void spmv(const olevel *L, const double *x, double *y) {
+  if (L->sum_order == 1) {
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < L->n; ++p) {
+      double s = 0.0;
+      for (long q = L->rowptr[p + 1] - 1; q >= L->rowptr[p]; --q) s += L->val[q] * x[L->col[q]];
+      y[p] = s;
+    }
+    return;
+  }
 #pragma omp parallel for schedule(static)
   for (long p = 0; p < L->n; ++p) {
     double s = 0.0;
@@ -202,7 +216,24 @@ static void spmv(const olevel *L, const double *x, double *y) {
   }
 }
 
-static double dot(long n, const double *a, const double *b) {
+/* Pairwise (cascade) sum of a[i] b[i]: halves summed recursively, runs of at
+ * most 8 products summed in index order.  Its rounding error is bounded by
+ * about (log2(n) + 8) u sum |a_i b_i| instead of the n u of the sequential
+ * sum; used only as the second summation order. */
+static double dot_pairwise(long n, const double *a, const double *b) {
+  if (n <= 8) {
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+  }
+  const long h = n / 2;
+  return dot_pairwise(h, a, b) + dot_pairwise(n - h, a + h, b + h);
+}
+
+/* a . b over n entries: a sequential sum in index order, or the pairwise sum
+ * when the level runs the second summation order. */
+static double dot(const olevel *L, long n, const double *a, const double *b) {
+  if (L->sum_order == 1) return dot_pairwise(n, a, b);
   double s = 0.0;
   for (long i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
@@ -378,16 +409,16 @@ static double lanczos_lmax(olevel *L) {
   for (long i = 0; i < n; ++i) r[i] = uniform01(ORC_EIG_SEED, 3, (uint64_t)i) - 0.5;
   for (long i = 0; i < n; ++i) z[i] = r[i] / L->diag[i];
   memcpy(p, z, sizeof(double) * n);
-  double rz = dot(n, r, z);
+  double rz = dot(L, n, r, z);
   int m = 0;
   for (int j = 0; j < ORC_EIG_STEPS && (long)j < n; ++j) {
     spmv(L, p, q);
-    const double pq = dot(n, p, q);
+    const double pq = dot(L, n, p, q);
     if (!(pq > 0.0) || !(rz > 0.0)) break;
     al[j] = rz / pq;
     for (long i = 0; i < n; ++i) r[i] -= al[j] * q[i];
     for (long i = 0; i < n; ++i) z[i] = r[i] / L->diag[i];
-    const double rz_new = dot(n, r, z);
+    const double rz_new = dot(L, n, r, z);
     be[j] = rz_new / rz;
     for (long i = 0; i < n; ++i) p[i] = z[i] + be[j] * p[i];
     rz = rz_new;
@@ -728,6 +759,23 @@ int orc_set_coarse(void *hh, int mode, double rtol, int maxit) {
 }
 
 /* Upper end of level l's Chebyshev interval. */
+/* Summation order of every level's dot products and operator rows: 0 (the
+ * default) sums in index order; 1 sums dot products pairwise and operator
+ * rows from the last stored entry to the first.  Both are fixed orders of the
+ * same arithmetic; running a solve under each measures how far rounding order
+ * alone moves its iterates (test infrastructure for the parity tolerances). */
+int orc_set_sum_order(void *hh, int order) {
+  ohier *H = (ohier *)hh;
+  if (order < 0 || order > 1) return -1;
+  for (int l = 0; l < H->L; ++l) H->lv[l].sum_order = order;
+  return 0;
+}
+
+/* a . b over n entries in the finest level's summation order. */
+double orc_dot(void *hh, long n, const double *a, const double *b) {
+  return dot(&((ohier *)hh)->lv[0], n, a, b);
+}
+
 double orc_level_beta(void *hh, int l) { return ((ohier *)hh)->lv[l].beta; }
 double orc_level_alpha(void *hh, int l) { return ((ohier *)hh)->lv[l].alpha; }
 
@@ -844,14 +892,14 @@ int orc_fgmres(void *hh, const double *ff, double *xf, double rtol, int maxit, i
   double *cs = (double *)malloc(sizeof(double) * m), *sn = (double *)malloc(sizeof(double) * m);
   double *g = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
   to_interior(L, ff, b);
-  const double bnorm = sqrt(dot(n, b, b));
+  const double bnorm = sqrt(dot(L, n, b, b));
   int it = 0, status = 0;
   double rnorm = bnorm;
   if (hist) hist[0] = bnorm > 0 ? 1.0 : 0.0;
   while (bnorm > 0.0) {
     spmv(L, x, w); /* restart from the true residual */
     for (long i = 0; i < n; ++i) r[i] = b[i] - w[i];
-    const double beta = sqrt(dot(n, r, r));
+    const double beta = sqrt(dot(L, n, r, r));
     rnorm = beta;
     if (beta <= rtol * bnorm || it >= maxit) break;
     for (long i = 0; i < n; ++i) V[i] = r[i] / beta;
@@ -862,13 +910,13 @@ int orc_fgmres(void *hh, const double *ff, double *xf, double rtol, int maxit, i
       double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
       vcycle(H, 0, vj, zj);
       spmv(L, zj, w);
-      for (int i = 0; i <= j; ++i) Hs[(size_t)i * m + j] = dot(n, w, V + (size_t)i * n);
+      for (int i = 0; i <= j; ++i) Hs[(size_t)i * m + j] = dot(L, n, w, V + (size_t)i * n);
       for (int i = 0; i <= j; ++i) {
         const double hij = Hs[(size_t)i * m + j];
         const double *vi = V + (size_t)i * n;
         for (long q = 0; q < n; ++q) w[q] -= hij * vi[q];
       }
-      const double hn = sqrt(dot(n, w, w));
+      const double hn = sqrt(dot(L, n, w, w));
       Hs[(size_t)(j + 1) * m + j] = hn;
       if (hn > 0.0)
         for (long q = 0; q < n; ++q) V[(size_t)(j + 1) * n + q] = w[q] / hn;
@@ -907,7 +955,7 @@ int orc_fgmres(void *hh, const double *ff, double *xf, double rtol, int maxit, i
   for (long i = 0; i < n; ++i) w[i] = b[i] - w[i];
   if (out) {
     out[0] = bnorm > 0 ? rnorm / bnorm : 0.0;
-    out[1] = bnorm > 0 ? sqrt(dot(n, w, w)) / bnorm : 0.0;
+    out[1] = bnorm > 0 ? sqrt(dot(L, n, w, w)) / bnorm : 0.0;
     out[2] = bnorm;
   }
   to_full(L, x, xf);
@@ -989,33 +1037,33 @@ int orc_pcg(void *hh, const double *ff, double *xf, double rtol, int maxit, int 
   double *q = (double *)malloc(sizeof(double) * n);
   to_interior(L, ff, b);
   if (nonzero_guess) to_interior(L, xf, x);
-  double bnorm = sqrt(dot(n, b, b));
+  double bnorm = sqrt(dot(L, n, b, b));
   spmv(L, x, q);
   for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
-  double rnorm = sqrt(dot(n, r, r));
+  double rnorm = sqrt(dot(L, n, r, r));
   int it = 0, status = 0;
   if (hist) hist[0] = bnorm > 0 ? rnorm / bnorm : 0.0;
   if (bnorm == 0.0 || rnorm <= rtol * bnorm) goto done;
   vcycle(H, 0, r, z);
   memcpy(p, z, sizeof(double) * n);
-  double rho = dot(n, r, z);
+  double rho = dot(L, n, r, z);
   for (it = 1; it <= maxit; ++it) {
     spmv(L, p, q);
-    double pq = dot(n, p, q);
+    double pq = dot(L, n, p, q);
     if (!(pq > 0.0)) { status = -1; break; }
     double alpha = rho / pq;
     for (long i = 0; i < n; ++i) {
       x[i] += alpha * p[i];
       r[i] -= alpha * q[i];
     }
-    rnorm = sqrt(dot(n, r, r));
+    rnorm = sqrt(dot(L, n, r, r));
     if (hist) hist[it] = rnorm / bnorm;
     if (rnorm <= rtol * bnorm) break;
     if (it == maxit) break;
     if (flexible) memcpy(zo, z, sizeof(double) * n);
     vcycle(H, 0, r, z);
-    double rho_new = dot(n, r, z);
-    double beta = flexible ? (rho_new - dot(n, r, zo)) / rho : rho_new / rho;
+    double rho_new = dot(L, n, r, z);
+    double beta = flexible ? (rho_new - dot(L, n, r, zo)) / rho : rho_new / rho;
     for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     rho = rho_new;
   }
@@ -1025,7 +1073,7 @@ done:
   for (long i = 0; i < n; ++i) q[i] = b[i] - q[i];
   if (out) {
     out[0] = bnorm > 0 ? rnorm / bnorm : 0.0;
-    out[1] = bnorm > 0 ? sqrt(dot(n, q, q)) / bnorm : 0.0;
+    out[1] = bnorm > 0 ? sqrt(dot(L, n, q, q)) / bnorm : 0.0;
     out[2] = bnorm;
   }
   to_full(L, x, xf);

@@ -682,3 +682,62 @@ def test_adjoint_identities():
     phm, _, _ = O.pcg(f - df, 1e-13)
     dL = 0.25 * (np.sum(php ** 2) - np.sum(phm ** 2))
     assert abs(dL - np.sum(lam * df)) <= 1e-8 * abs(dL)
+
+
+# ------------------------------------------------------------------ second summation order
+# The oracle can run every dot product as a pairwise sum and every operator
+# row in decreasing column order (sum_order=1).  The method fixes no
+# summation order: sequential and pairwise float64 sums are both faithful
+# readings of it.  The two fixed orders measure how far rounding order alone
+# moves a solve, which is the evidence behind the GPU parity tolerances.
+# These pins fix both orders against exact sums (math.fsum is correctly
+# rounded) and their textbook error bounds.
+def test_dot_products_in_both_orders_meet_their_error_bounds():
+    u = 2.0 ** -53
+    O0 = oracle.Oracle(np.ones((4, 4, 4)), levels=1)
+    O1 = oracle.Oracle(np.ones((4, 4, 4)), levels=1, sum_order=1)
+    rng = np.random.default_rng(11)
+    differs = False
+    for n in (1, 7, 8, 9, 1000, 100003):
+        a = rng.standard_normal(n) * np.exp(rng.uniform(-20, 20, n))
+        b = rng.standard_normal(n)
+        b[: n // 2] = -a[: n // 2] * (1.0 + 1e-3 * rng.standard_normal(n // 2))  # heavy cancellation
+        exact = math.fsum(x * y for x, y in zip(a.tolist(), b.tolist()))  # products rounded once, as in both orders
+        mag = float(np.sum(np.abs(a * b)))
+        s0, s1 = O0.dot(a, b), O1.dot(a, b)
+        assert abs(s0 - exact) <= n * u * mag * 1.01 + 1e-300
+        assert abs(s1 - exact) <= (math.ceil(math.log2(max(n, 2))) + 8) * u * mag * 1.01 + 1e-300
+        differs |= s0 != s1
+    assert differs  # the second order is a different order, not the same sum again
+
+
+def test_operator_rows_in_both_orders_meet_their_error_bounds():
+    """Rows of A x summed in increasing and in decreasing column order: each
+    within 7u sum_j |a_ij x_j| of the exact row sum of the same stored entries."""
+    dims = (9, 17, 9)
+    k = mi.cell_k(dims, 2, -3.0, 3.0, 12)
+    O0 = oracle.Oracle(k, levels=1)
+    O1 = oracle.Oracle(k, levels=1, sum_order=1)
+    x = mi.random_nodal(dims, 13)
+    rp, col, val = O0.csr()
+    xi = interior(x).ravel()
+    exact = np.array([math.fsum((val[q] * xi[col[q]]) for q in range(rp[p], rp[p + 1])) for p in range(len(rp) - 1)])
+    mag = np.array([np.sum(np.abs(val[rp[p]:rp[p + 1]] * xi[col[rp[p]:rp[p + 1]]])) for p in range(len(rp) - 1)])
+    y0 = interior(O0.apply(x)).ravel()
+    y1 = interior(O1.apply(x)).ravel()
+    u = 2.0 ** -53
+    assert np.all(np.abs(y0 - exact) <= 7 * u * mag * 1.01)
+    assert np.all(np.abs(y1 - exact) <= 7 * u * mag * 1.01)
+    assert np.any(y0 != y1)
+
+
+def test_second_summation_order_solves_the_same_problem():
+    """Both orders run the same algorithm: on a moderate-contrast problem they
+    take the same iterations to the same solution up to rounding."""
+    dims = (17, 17, 17)
+    k = mi.cell_k(dims, 4, -1.0, 1.0, 14)
+    f = mi.rhs_f(dims, 14)
+    x0, i0, _ = oracle.Oracle(k).pcg(f, 1e-10)
+    x1, i1, _ = oracle.Oracle(k, sum_order=1).pcg(f, 1e-10)
+    assert i0 == i1
+    assert np.linalg.norm(x1 - x0) <= 1e-12 * np.linalg.norm(x0)
