@@ -5,7 +5,14 @@ One step = one full solve of the 257^3-vertex workload (log10 k ~ U[-2,2] on
 dense Cholesky on the 3^3 coarsest level, float64 CG to ||r|| <= 1e-8 ||f||)
 with inputs resident on the GPU.  The headline form runs the V-cycle in
 float32 inside the float64 CG; the plain float64 form and the bfloat16-
-coefficient form are timed the same way and reported beside it.
+coefficient form are timed the same way and reported beside it, each with its
+relative error against the CPU float64 oracle's solution of the same problem.
+
+The same line carries the 513^3 contrast-10^6 target solve with Galerkin
+coarse operators (north_star_target), the paper's solver configurations, the
+end-to-end figure through the C ABI with host buffers, the per-iteration host
+round trip, and the oracle timed on the host cores (a full solve, the second
+of two identical ones).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own independent problem (seed + rank):
@@ -144,7 +151,7 @@ def whole_job_dofs_per_s(unknowns_per_rank: int, world: int, ms_per_step: float)
     return world * unknowns_per_rank / (ms_per_step * 1e-3)
 
 
-def config_dict(spec, n_ranks, iters=None, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised"):
+def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised"):
     N = spec["N"]
     levels = 1
     M = N
@@ -157,19 +164,20 @@ def config_dict(spec, n_ranks, iters=None, name=None, face_rule=0, adjoint=False
                     f"edge k, {levels} levels ({'Galerkin R A P' if coarse_op == 'galerkin' else 're-discretised'} coarse "
                     f"operators), V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual "
                     f"{spec['rtol']:g}" + ("; step = forward + adjoint solve with the cell gradient" if adjoint else ""),
-        "precision": HEADLINE,
         "l2": "no flush: inputs larger than L2 (each float64 vector 134 MB; working set > 2 GB)",
         "parallelism": "replicas" if n_ranks > 1 else "single GPU",
     }
-    if iters is not None:
-        d["iterations"] = iters
     return d
 
 
 # ------------------------------------------------------------------ oracle arms
+def oracle_cores() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
 def oracle_sample(spec, iters_to_tol: int, sample_iters: int):
     """Time `sample_iters` oracle PCG iterations on the full workload; return
-    (DOF/s to tolerance, seconds, cores)."""
+    (DOF/s to tolerance extrapolated by the iteration count, seconds, cores)."""
     import oracle
     dims = (spec["N"],) * 3
     k = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], spec["seed"])
@@ -179,8 +187,19 @@ def oracle_sample(spec, iters_to_tol: int, sample_iters: int):
     O.pcg(f, 0.0, maxit=sample_iters)
     dt = time.perf_counter() - t
     n = (spec["N"] - 2) ** 3
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return n / (dt / sample_iters * iters_to_tol), dt, cores
+    return n / (dt / sample_iters * iters_to_tol), dt, oracle_cores()
+
+
+def oracle_full_solve(k, f, rtol):
+    """The oracle's solve of the workload to tolerance, run twice with the
+    second timed (the paper's protocol of timing the second of two identical
+    solves).  Returns (solution, iterations, seconds of the second solve)."""
+    import oracle
+    O = oracle.Oracle(k)
+    O.pcg(f, rtol, maxit=3000)
+    t = time.perf_counter()
+    x, it, _ = O.pcg(f, rtol, maxit=3000)
+    return x, it, time.perf_counter() - t
 
 
 def golden_iterations():
@@ -202,13 +221,16 @@ def run_reference(args):
             vals.append(v)
             times.append(dt)
     value = float(np.median(vals))
-    desc = (f"CPU FP64 oracle (assembled CSR, OpenMP) on the full {spec['N']}^3 workload: {sample} PCG iterations "
-            f"per step, scaled by its {its}-iteration count to tolerance")
+    desc = (f"CPU FP64 oracle (assembled CSR, OpenMP) on the full {spec['N']}^3 workload: each step times "
+            f"{sample} PCG iterations and the value is EXTRAPOLATED to a solve by its recorded {its}-iteration count "
+            f"to tolerance (a full solve per step would take about 20 s on 16 cores; the full-solve figure is the "
+            f"GPU arm's cpu_baseline)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(spec, 1, its),
+        "precision": "fp64 (CPU oracle)", "iterations": its,
+        "config": config_dict(spec, 1),
         "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -231,8 +253,10 @@ def run_ours(args):
     seed = replica_seed(spec, rank)
     dims = (spec["N"],) * 3
     n = (spec["N"] - 2) ** 3
-    k = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed), device=dev)
-    f_host = torch.tensor(mi.rhs_f(dims, seed)).pin_memory()
+    k_np = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed)
+    f_np = mi.rhs_f(dims, seed)
+    k = torch.tensor(k_np, device=dev)
+    f_host = torch.tensor(f_np).pin_memory()
     f = f_host.to(dev)
     rtol = spec["rtol"]
 
@@ -242,18 +266,24 @@ def run_ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    def timed(fn, steps):
+        """Device time of `steps` calls of fn (CUDA events on the current
+        stream, barrier and synchronize on both sides), max over ranks, ms
+        per call."""
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = [fn() for _ in range(steps)]
+        e1.record()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1), dev) / steps, out
 
     forms = {}
     solutions = {}
-    roofline = smoother = clocks = None
+    roofline = smoother = clocks = host_gap = e2e = None
     launches = 0
     run_forms = [HEADLINE] + [fm for fm in args.forms.split(",") if fm in FORMS and fm != HEADLINE]
-    def step(S):
-        x, st = S.solve(f, rtol, raise_on_error=False)
-        if args.adjoint:
-            g = x - phi_obs if phi_obs is not None else x
-            lam, grad, _ = S.solve_adjoint(g.contiguous(), rtol, x)
-        return x, st
 
     phi_obs = None
     if args.adjoint:  # loss 0.5 |phi - phi_obs|^2 with phi_obs from the k field of seed + 1
@@ -264,7 +294,13 @@ def run_ours(args):
         So.close()
         del So
 
-    for form in run_forms:
+    def step(S):
+        x, st = S.solve(f, rtol, raise_on_error=False)
+        if args.adjoint:
+            S.solve_adjoint((x - phi_obs).contiguous(), rtol, x)
+        return x, st
+
+    for form in (run_forms if not args.only_paper_configs else []):
         S = mg.MGSolver(k, mg.Params(precision=form, maxit=args.maxit, face_rule=args.face_rule,
                                      coarse_op=args.coarse_op))
         headline = form == HEADLINE
@@ -272,31 +308,22 @@ def run_ours(args):
         for w in range(args.warmup):
             if headline and w == 0:
                 S.timing(True)  # one fully instrumented warm-up solve: per-kernel breakdown
-            x, st = step(S)
+            step(S)
             if headline and w == 0:
                 profile_all = S.kernel_times()
                 S.timing(False)
         if headline:
-            dom = max(((c, v[0]) for (c, l), v in profile_all.items() if l == 0), key=lambda t: t[1])[0]
+            dom = max(((c, v[0]) for (c, l), v in profile_all.items() if l == 0 and c != "host_gap"),
+                      key=lambda t: t[1])[0]
             sampler = ClockSampler(dev.index if dev.index is not None else 0)
             sampler.start()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        iters = []
-        launches_form = 0
-        for _ in range(args.steps):
-            x, st = step(S)
-            iters.append(st.iters)
-            launches_form += st.kernel_launches
-        e1.record()
-        barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
-        forms[form] = {"value": whole_job_dofs_per_s(n, world, ms), "ms_per_step": ms, "iters": iters[-1],
+        ms, outs = timed(lambda: step(S), args.steps)
+        x, st = outs[-1]
+        forms[form] = {"value": whole_job_dofs_per_s(n, world, ms), "ms_per_step": ms, "iters": st.iters,
                        "true_rel_resid": st.true_rel_resid, "status": st.status}
         solutions[form] = x.detach().clone()
         if headline:
+            launches = sum(o[1].kernel_launches for o in outs)
             # the same K steps again with CUDA events around every launch of the
             # dominant finest-level kernel class and of the smoother steps (events
             # inside the V-cycle graph slow the whole solve, so the headline steps
@@ -305,47 +332,52 @@ def run_ours(args):
             for _ in range(args.steps):
                 S.solve(f, rtol, raise_on_error=False)
             torch.cuda.synchronize()
-            clocks = sampler.stop()
-            launches = launches_form
             kt = S.kernel_times()
+            # and once more timing only the host round trip between outer
+            # iterations (the V-cycle still replays from its graph)
+            S.timing(True, classes=["host_gap"], levels=[0])
+            ms_gap_run, gouts = timed(lambda: S.solve(f, rtol, raise_on_error=False), args.steps)
+            gt = S.kernel_times().get(("host_gap", 0))
             S.timing(False)
+            clocks = sampler.stop()
             roofline = roofline_from(kt, form, clocks, dom, args.workload)
             smoother = roofline_from(kt, form, clocks, "cheb_step", args.workload)
+            if gt:
+                gap_ms, gap_n, _ = gt
+                host_gap = {"us_per_iteration": 1e3 * gap_ms / gap_n, "ms_per_solve": gap_ms / args.steps,
+                            "share_of_solve": (gap_ms / args.steps) / ms_gap_run, "iterations_measured": gap_n,
+                            "what": "device time from the end of an outer iteration's last kernel to the next "
+                                    "V-cycle launch (read of the CG scalars, host convergence test, next launch), "
+                                    "V-cycle replayed from its CUDA graph"}
             forms[form]["kernel_ms_per_solve_warmup_profile"] = {f"{c}@L{l}": round(v[0], 4)
                                                                   for (c, l), v in profile_all.items()}
-            # end to end: pinned host f -> device, solve, x -> pinned host, every step
+            # end to end through the C ABI with HOST buffers: the library copies the
+            # pinned f in and x out inside every call
             x_host = torch.empty(dims, dtype=torch.float64).pin_memory()
-            fd = torch.empty_like(f)
-            barrier()
-            e0.record()
-            for _ in range(args.steps):
-                fd.copy_(f_host, non_blocking=True)
-                xe, _ = S.solve(fd, rtol, raise_on_error=False)
-                if args.adjoint:
+            S.solve_host(f_host, x_host, rtol, raise_on_error=False)  # first call allocates the staging arrays
+            if args.adjoint:
+                def e2e_step():
+                    S.solve_host(f_host, x_host, rtol, raise_on_error=False)
+                    xe = x_host.to(dev, non_blocking=True)
                     S.solve_adjoint((xe - phi_obs).contiguous(), rtol, xe)
-                x_host.copy_(xe, non_blocking=True)
-            e1.record()
-            barrier()
-            ms_e2e = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+            else:
+                def e2e_step():
+                    S.solve_host(f_host, x_host, rtol, raise_on_error=False)
+            ms_e2e, _ = timed(e2e_step, args.steps)
             e2e = {"value": whole_job_dofs_per_s(n, world, ms_e2e), "unit": "DOF/s",
-                   "h2d_bytes_per_step": f_host.numel() * 8, "d2h_bytes_per_step": x_host.numel() * 8}
+                   "h2d_bytes_per_step": f_host.numel() * 8, "d2h_bytes_per_step": x_host.numel() * 8,
+                   "api": "mg_solve_host (C ABI, pinned host f and x)"}
         S.close()
         del S
+
     def timed_variant(**extra):
         """The headline precision with other method choices, on the same problem
         and tolerance, timed like the forms above."""
         S = mg.MGSolver(k, mg.Params(precision=HEADLINE, maxit=args.maxit, face_rule=args.face_rule, **extra))
         for _ in range(args.warmup):
             S.solve(f, rtol, raise_on_error=False)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            xg, stg = S.solve(f, rtol, raise_on_error=False)
-        e1.record()
-        barrier()
-        msg = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+        msg, outs = timed(lambda: S.solve(f, rtol, raise_on_error=False), args.steps)
+        stg = outs[-1][1]
         out = {"value": whole_job_dofs_per_s(n, world, msg), "unit": "DOF/s", "ms_per_step": msg,
                "iters": stg.iters, "true_rel_resid": stg.true_rel_resid, "status": stg.status,
                "precision": HEADLINE, **{k_: v_ for k_, v_ in extra.items() if k_ != "maxit"}}
@@ -369,6 +401,13 @@ def run_ours(args):
                 coarse_solve="gmres", coarse_rtol=1e-4),
             "fgmres_rediscretised_chebyshev10": timed_variant(krylov="fgmres", cheby_degree=10),
         }
+    if args.only_paper_configs:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": "DOF/s", "galerkin_coarse_operators": galerkin,
+                              "paper_configurations": paper, "config": config_dict(spec, world, args.workload)}),
+                  flush=True)
+        return
+
     speedup = None
     if "fp64" in solutions:
         ref = solutions["fp64"]
@@ -377,32 +416,89 @@ def run_ours(args):
                 forms[form]["rel_err_vs_fp64_gpu"] = float((solutions[form] - ref).norm() / ref.norm())
         speedup = forms["fp64"]["ms_per_step"] / forms[HEADLINE]["ms_per_step"]
 
+    target = None
+    if (world == 1 and not args.no_north_star and args.workload == WORKLOAD and not args.adjoint
+            and args.coarse_op == "rediscretised"):
+        target = north_star_target(args, dev, timed)
+
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.adjoint
             and args.coarse_op == "rediscretised"):
-        its = forms.get("fp64", forms[HEADLINE])["iters"]
-        # about 12 s of PCG iterations on the 16 host cores of a GB300 machine
-        # (0.15 s per iteration there), never more than the solve takes
-        sample = min(80, its)
-        v, dt, cores = oracle_sample(spec, its, sample)
-        cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
-               "sample": f"{sample} PCG iterations of the CPU FP64 oracle on the full {spec['N']}^3 workload "
-                         f"({dt:.1f} s), scaled by the {its}-iteration count to tolerance"}
+        xo, ito, dt = oracle_full_solve(k_np, f_np, rtol)
+        cpu = {"value": n / dt, "unit": "DOF/s", "cores": oracle_cores(), "kind": "oracle",
+               "iterations": ito, "seconds": dt,
+               "sample": f"full solve of the {spec['N']}^3 workload to rel. residual {rtol:g} by the CPU FP64 "
+                         f"oracle ({ito} PCG iterations, {dt:.1f} s), the second of two identical solves"}
+        xo_norm = np.linalg.norm(xo)
+        for form, xs in solutions.items():
+            forms[form]["rel_err_vs_oracle"] = float(np.linalg.norm(xs.cpu().numpy() - xo) / xo_norm)
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": forms[HEADLINE]["value"], "unit": "DOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms[HEADLINE]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic", "config": config_dict(spec, world, forms[HEADLINE]["iters"], args.workload,
-                                                   args.face_rule, args.adjoint, args.coarse_op),
-        "forms": forms, "speedup_mixed_vs_fp64": speedup, "galerkin_coarse_operators": galerkin,
-        "paper_configurations": paper,
-        "roofline": roofline, "smoother_roofline": smoother, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        "data": "synthetic", "precision": HEADLINE, "iterations": forms[HEADLINE]["iters"],
+        "config": config_dict(spec, world, args.workload, args.face_rule, args.adjoint, args.coarse_op),
+        "forms": forms, "speedup_mixed_vs_fp64": speedup, "north_star_target": target,
+        "galerkin_coarse_operators": galerkin, "paper_configurations": paper,
+        "roofline": roofline, "smoother_roofline": smoother, "host_gap": host_gap, "cpu_baseline": cpu,
+        "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def north_star_target(args, dev, timed):
+    """The 513^3 contrast-10^6 target with Galerkin coarse operators: the
+    float32-V-cycle and float64 forms, one warm-up and two timed solves each,
+    their iterations and true residuals (also from the oracle's own operator),
+    the speed-up of the mixed form at equal final accuracy, and the smoother
+    step's HBM roofline at this size."""
+    import torch
+    import oracle
+    import paper_1604_07163_gb300 as mg
+    name = "poisson513_c1e6"
+    spec = dict(mi.WORKLOADS[name])
+    dims = (spec["N"],) * 3
+    n = (spec["N"] - 2) ** 3
+    k_np = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], spec["seed"])
+    f_np = mi.rhs_f(dims, spec["seed"])
+    k = torch.tensor(k_np, device=dev)
+    f = torch.tensor(f_np, device=dev)
+    out = {"workload": config_dict(spec, 1, name, coarse_op="galerkin")["workload"], "steps": 2, "warmup": 1,
+           "forms": {}}
+    xs = {}
+    for form in ("mixed_fp32", "fp64"):
+        S = mg.MGSolver(k, mg.Params(precision=form, coarse_op="galerkin", maxit=args.maxit))
+        S.solve(f, spec["rtol"], raise_on_error=False)
+        ms, outs = timed(lambda: S.solve(f, spec["rtol"], raise_on_error=False), 2)
+        x, st = outs[-1]
+        out["forms"][form] = {"value": n / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms, "iters": st.iters,
+                              "true_rel_resid": st.true_rel_resid, "status": st.status,
+                              "setup_s": st.setup_s}
+        if form == "mixed_fp32":
+            S.timing(True, classes=["cheb_step"], levels=[0])
+            S.solve(f, spec["rtol"], raise_on_error=False)
+            torch.cuda.synchronize()
+            out["smoother_roofline"] = roofline_from(S.kernel_times(), form, None, "cheb_step", name)
+            S.timing(False)
+        xs[form] = x.cpu().numpy()
+        del x, outs
+        S.close()
+        del S
+        torch.cuda.empty_cache()
+    del k, f
+    torch.cuda.empty_cache()
+    O = oracle.Oracle(k_np)  # the finest operator is the same under either coarse-operator choice
+    fn = np.linalg.norm(f_np)
+    for form, xv in xs.items():
+        r = (f_np - O.apply(xv))[1:-1, 1:-1, 1:-1]
+        out["forms"][form]["true_rel_resid_by_oracle"] = float(np.linalg.norm(r) / fn)
+    out["rel_err_mixed_vs_fp64_gpu"] = float(np.linalg.norm(xs["mixed_fp32"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
+    out["speedup_mixed_vs_fp64"] = out["forms"]["fp64"]["ms_per_step"] / out["forms"]["mixed_fp32"]["ms_per_step"]
+    return out
 
 
 # float64 operations per point of the float64-pipe-bound outer-CG kernel
@@ -512,6 +608,10 @@ def main():
                     help="skip the extra timing of the headline form with Galerkin coarse operators")
     ap.add_argument("--no-paper-configs", action="store_true",
                     help="skip timing the solver configurations of the paper's experiments")
+    ap.add_argument("--no-north-star", action="store_true",
+                    help="skip the 513^3 contrast-10^6 Galerkin target solve")
+    ap.add_argument("--only-paper-configs", action="store_true",
+                    help="time only the Galerkin variant and the paper's solver configurations (for profiling)")
     ap.add_argument("--maxit", type=int, default=3000)
     ap.add_argument("--adjoint", action="store_true", help="each step is a forward + adjoint solve with gradient")
     args = ap.parse_args()

@@ -104,12 +104,10 @@ typedef struct {
                             thread: vector loads, x neighbours by warp shuffles, z neighbours
                             in registers, L2 prefetch two planes ahead (the fastest measured
                             on GB300),
-                          1 as 0, plus the coarse-grid correction folded into the first
-                            post-smoothing step (shared-plane z-marching kernel) on levels with at
-                            least 64 points per axis,
-                          2 TMA-staged tiles (cp.async.bulk.tensor),
-                          3 shared-plane z-marching for every pass,
-                          4 z-marching with one point per thread and neighbours read through L1 */
+                          1 TMA-staged tiles (cp.async.bulk.tensor into an mbarrier-tracked ring of
+                            shared-memory stages; every wait bounded),
+                          2 z-marching with one point per thread and neighbours read through L1 (the
+                            driver the float64 CG operator and the 27-point passes always use) */
   int use_pdl;         /* 1: launch solve kernels as programmatic dependent launches (default 1) */
   int smoother;        /* mg_smoother (default MG_SMOOTHER_CHEBYSHEV).  With Richardson, nu_pre and
                           nu_post count iterations and cheby_degree, eig_lo_frac, eig_hi are unused */
@@ -134,6 +132,15 @@ typedef struct {
   int bottom_blocks;   /* blocks of the bottom kernel: 0 (default) chosen from the size of its finest
                           level; 1 one block; 2, 4 or 8 one thread-block cluster that splits every pass.
                           The result is bitwise the same for every choice */
+  int test_inject;     /* TEST ONLY: a data perturbation made by the host at setup so that the error paths
+                          can be exercised without any GPU fault.  0 (default) none; 1 the float64 finest
+                          diagonal used by the outer Krylov operator is negated, so p.Ap < 0 and mg_solve
+                          returns MG_ERR_BREAKDOWN in its first iteration; 2 the diagonal of the dense
+                          coarsest operator is negated before its Cholesky factorisation, so mg_setup returns
+                          MG_ERR_NOT_SPD; 3 the bounded waits of the TMA-staged kernels (stencil_kernel 1)
+                          give up without polling, so every block sets the timeout flag, drains the copies
+                          it issued (with the full poll limit) and returns, and mg_solve returns
+                          MG_ERR_DEVICE_TIMEOUT */
 } mg_params;
 
 typedef struct {
@@ -177,6 +184,16 @@ mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_sta
  * dL/df equals lambda.  grad_logk is a device cell array. */
 mg_status mg_solve_adjoint(mg_handle* h, const double* g, double* lambda, double rtol,
                            const double* phi, double* grad_logk, mg_stats* st);
+
+/* mg_solve with HOST buffers: f_host and x_host are host nodal arrays (pinned
+ * memory gives full-bandwidth copies; pageable memory works, more slowly).
+ * The call copies f to the device, solves (x_host is read as the initial
+ * guess when the handle was built with nonzero_guess), copies x back and
+ * synchronises the stream, all on the handle's stream.  The first call
+ * allocates two device nodal arrays of the finest grid, kept by the handle
+ * until mg_free.  Errors as mg_solve; on MG_ERR_NOT_CONVERGED x_host holds the
+ * last iterate. */
+mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, double rtol, mg_stats* st);
 
 /* Release every buffer the handle owns.  h may be NULL. */
 mg_status mg_free(mg_handle* h);
@@ -242,7 +259,11 @@ mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, doubl
  *    capture.
  *  - Every call shares the one static array (per device): calls that overlap
  *    on the GPU (different streams or handles at the same time) race.  Each
- *    call writes every partial it later reads, so no clearing is needed. */
+ *    call writes every partial it later reads, so no clearing is needed.
+ *  - The device address of the array is cached per device index for the
+ *    life of the process; it does not survive cudaDeviceReset (or any other
+ *    teardown of the device's primary context), after which this entry point
+ *    must not be called again. */
 #define MG_NOALLOC_MAX_PLANES 4096
 mg_status mg_residual_norm_noalloc(mg_handle* h, const double* f, const double* x, double* out);
 
@@ -250,9 +271,11 @@ mg_status mg_residual_norm_noalloc(mg_handle* h, const double* f, const double* 
  * When enabled, every launch of a kernel class in class_mask (bit c = class c)
  * on a level in level_mask (bit l = level l) is bracketed by CUDA events on
  * the launching stream and its device time is accumulated per class and
- * level.  class_mask = 0 disables timing.  While timing is on the V-cycle is
+ * level.  class_mask = 0 disables timing.  While a class run inside the
+ * V-cycle (MG_K_CHEB_ZERO .. MG_K_BOTTOM, MG_K_DOT) is timed, the V-cycle is
  * launched kernel by kernel (not from the graph) so that the events are plain
- * stream events.  Enabling or disabling resets the counters. */
+ * stream events; timing only other classes keeps the graph.  Enabling or
+ * disabling resets the counters. */
 typedef enum {
   MG_K_CHEB_ZERO = 0,  /* smoother steps 0-1 from a zero guess (pre-smooth) */
   MG_K_CHEB_STEP = 1,  /* smoother step with a materialised iterate */
@@ -265,7 +288,10 @@ typedef enum {
   MG_K_DOT = 8,        /* r.z (float64 accumulation) */
   MG_K_CAST = 9,       /* float64 residual -> float32 V-cycle right-hand side */
   MG_K_CG_APPLY = 10,  /* q = A p, p.q with the float64 outer operator */
-  MG_K_NCLASS = 11
+  MG_K_HOST_GAP = 11,  /* not a kernel: per outer CG iteration, the device time from the end of the
+                          iteration's last kernel to the next V-cycle's launch, i.e. the read of the CG
+                          scalars by the host, its convergence test and its next launch (points = 0) */
+  MG_K_NCLASS = 12
 } mg_kernel_class;
 mg_status mg_timing_enable(mg_handle* h, int class_mask, int level_mask);
 /* Totals for class cls on level l (0 = finest): device milliseconds, number of

@@ -16,7 +16,6 @@
 #include "mg.h"
 #include "mg_kernels.cuh"
 #include "mg_tma.cuh"
-#include "mg_zs.cuh"
 #include "mg_zvec.cuh"
 #include "mg_g27.cuh"
 #include "mg_krylov.cuh"
@@ -36,9 +35,6 @@ struct LevelBuf {
   void* x[2] = {nullptr, nullptr};
   void *d = nullptr, *b = nullptr, *r = nullptr;
   // TMA tensor maps (2-D row views) for the staged stencil kernels
-  bool zs = false;         // 2.5-D shared-plane z-marching kernels for every stencil pass
-  bool zs_prolong = false; // 2.5-D kernel only for the correction folded into the first post-smoothing step
-  int zs_grid[3] = {0, 0, 0}, zs_kchunk = 0;
   bool tma = false;
   CUtensorMap m_full_x[2], m_full_b, m_full_dinv, m_kx, m_ky, m_kz, m_c_dinv, m_c_b, m_c_d, m_c_r64;
   int tma_grid[3] = {0, 0, 0}, tma_kchunk = 0;
@@ -110,6 +106,8 @@ struct mg_handle {
   int ev_graph_end = 0;  // events [0, ev_graph_end) belong to the captured graph
   int ev_next = 0;
   std::vector<TRec> graph_recs, pending;
+  cudaEvent_t gap_ev[2][2] = {};  // host-gap timing: two alternating (end of iteration, next launch) pairs
+  double* hstage[2] = {nullptr, nullptr};  // dense device nodal arrays of mg_solve_host (f, x)
   double t_ms[MG_K_NCLASS][MG_MAX_LEVELS] = {};
   long long t_n[MG_K_NCLASS][MG_MAX_LEVELS] = {};
   double t_pts[MG_K_NCLASS][MG_MAX_LEVELS] = {};
@@ -537,35 +535,11 @@ template <class TV, class TC> struct Impl {
     a.dinv_theta = inv_theta;
     a.partials = h->partials;
     a.status = &h->dsc->status;
+    a.poll_limit = h->prm.test_inject == 3 ? 0 : TMA_POLL_LIMIT;
     using Lay = TmaLayout<KIND, HAS_D, DOT, TV, TC>;
     dim3 grid(Lv.tma_grid[0], Lv.tma_grid[1], Lv.tma_grid[2]);
     const int e = tm_begin(h, cls, l);
     launch(h, k_tma_stencil<KIND, HAS_D, DOT, TV, TC>, grid, dim3(TT_THREADS), Lay::SMEM, maps, a);
-    ++h->launches;
-    tm_end(h, e, cls, l, (double)Lv.g.npts());
-    return grid.x * grid.y * grid.z;
-  }
-
-  // ---- 2.5-D shared-plane z-marching launches ---------------------------------
-  static void zs_prepare(mg_handle* h, int l) {
-    LevelBuf& Lv = h->lv[l];
-    const Geom& g = Lv.g;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zs<PolProlongStep0<TV, TV, TC>>, ZS_THREADS, 0);
-    per_sm = per_sm < 1 ? 1 : per_sm;
-    const int gx = (g.nx + ZS_TX - 1) / ZS_TX, gy = (g.ny + ZS_TY - 1) / ZS_TY;
-    const int zs = best_zsplit(gx * gy, h->nsm * per_sm, g.nz, 16);
-    Lv.zs_kchunk = (g.nz + zs - 1) / zs;
-    Lv.zs_grid[0] = gx;
-    Lv.zs_grid[1] = gy;
-    Lv.zs_grid[2] = (g.nz + Lv.zs_kchunk - 1) / Lv.zs_kchunk;
-  }
-
-  template <class Pol> static int zs_launch(mg_handle* h, int l, const Pol& pol, int cls) {
-    LevelBuf& Lv = h->lv[l];
-    dim3 grid(Lv.zs_grid[0], Lv.zs_grid[1], Lv.zs_grid[2]);
-    const int e = tm_begin(h, cls, l);
-    launch(h, k_zs<Pol>, grid, dim3(ZS_THREADS), 0, pol, Lv.g, Lv.zs_kchunk, h->partials);
     ++h->launches;
     tm_end(h, e, cls, l, (double)Lv.g.npts());
     return grid.x * grid.y * grid.z;
@@ -594,16 +568,7 @@ template <class TV, class TC> struct Impl {
       TV* dout = j + 1 < p.cheby_degree ? V(Lv.d) : nullptr;
       const TV* dprev = j > 0 ? V(Lv.d) : nullptr;
       int nb = -1;
-      if (Lv.zs) {
-        if (dot)
-          nb = zs_launch(h, l, PolStep<TV, TV, TC, true>{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx),
-                                                         C(Lv.ky), C(Lv.kz), h->cr, (TV)c1, (TV)c2, inv_theta},
-                         MG_K_CHEB_STEP);
-        else
-          zs_launch(h, l, PolStep<TV, TV, TC, false>{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx),
-                                                      C(Lv.ky), C(Lv.kz), nullptr, (TV)c1, (TV)c2, inv_theta},
-                    MG_K_CHEB_STEP);
-      } else if (Lv.tma) {
+      if (Lv.tma) {
         const CUtensorMap& f0 = Lv.m_full_x[cur];
         if (j > 0 && dot) nb = tma_launch<TK_STEP, true, true>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
         else if (j > 0) tma_launch<TK_STEP, true, false>(h, l, f0, nullptr, xo, dout, c1, c2, 1.0 / theta, MG_K_CHEB_STEP);
@@ -643,7 +608,7 @@ template <class TV, class TC> struct Impl {
       return cur ^ 1;
     }
     if constexpr (std::is_same<TV, double>::value) {
-      if (!Lv.zs && !Lv.tma) {  // store step 0, then step 1 as an ordinary step (OpChebStart)
+      if (!Lv.tma) {  // store step 0, then step 1 as an ordinary step (OpChebStart)
         OpChebStart<TV, TV> op{V(Lv.b), V(Lv.dinv), V(Lv.x[cur]), V(Lv.d), inv_theta};
         zmarch<false>(h, Lv.g, op, MG_K_CHEB_ZERO, l);
         return cheb_steps(h, l, cur, 1, 1.0 / sigma, fuse_rz);
@@ -653,11 +618,7 @@ template <class TV, class TC> struct Impl {
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
     const double c1 = rho * rho_prev, c2 = 2.0 * rho / delta;
     TV* dout = p.cheby_degree > 2 ? V(Lv.d) : nullptr;
-    if (Lv.zs) {
-      zs_launch(h, l, PolZero<TV, TV, TC>{V(Lv.b), V(Lv.dinv), V(Lv.x[cur ^ 1]), dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
-                                          (TV)c1, (TV)c2, inv_theta},
-                MG_K_CHEB_ZERO);
-    } else if (Lv.tma) {
+    if (Lv.tma) {
       tma_launch<TK_ZERO, false, false>(h, l, Lv.m_full_b, &Lv.m_full_dinv, V(Lv.x[cur ^ 1]), dout, c1, c2,
                                         1.0 / theta, MG_K_CHEB_ZERO);
     } else if (Lv.g27) {
@@ -673,24 +634,11 @@ template <class TV, class TC> struct Impl {
   }
 
   // Coarse-grid correction x += P e followed by the post-smoothing sweeps of
-  // level l.  On the 2.5-D kernels the correction is folded into the first
-  // smoother step (u = x + P e is formed per point, x + P e is never stored).
+  // level l.
   static int correct_and_post_smooth(mg_handle* h, int l, int cur, int ccur, bool fuse_rz) {
     LevelBuf& Lv = h->lv[l];
     LevelBuf& Cv = h->lv[l + 1];
     const mg_params& p = h->prm;
-    const bool single_step_dot = fuse_rz && p.nu_post == 1 && p.cheby_degree == 1;
-    if ((Lv.zs || Lv.zs_prolong) && p.nu_post >= 1 && !single_step_dot) {
-      double theta, delta, sigma;
-      cheb_consts(p, Lv.beta, Lv.alpha, &theta, &delta, &sigma);
-      zs_launch(h, l, PolProlongStep0<TV, TV, TC>{Cv.g, V(Lv.x[cur]), V(Cv.x[ccur]), V(Lv.b), V(Lv.dinv),
-                                                  V(Lv.x[cur ^ 1]), p.cheby_degree > 1 ? V(Lv.d) : nullptr,
-                                                  C(Lv.kx), C(Lv.ky), C(Lv.kz), (TV)(1.0 / theta)},
-                MG_K_PROLONG);
-      cur = cheb_steps(h, l, cur ^ 1, 1, 1.0 / sigma, fuse_rz && p.nu_post == 1);
-      for (int s = 1; s < p.nu_post; ++s) cur = sweep(h, l, cur, false, fuse_rz && s + 1 == p.nu_post);
-      return cur;
-    }
     OpProlong<TV, TV> pr{Cv.g, V(Cv.x[ccur]), V(Lv.x[cur])};
     zmarch<false>(h, Lv.g, pr, MG_K_PROLONG, l);
     for (int s = 0; s < p.nu_post; ++s) cur = sweep(h, l, cur, false, fuse_rz && s + 1 == p.nu_post);
@@ -763,9 +711,7 @@ template <class TV, class TC> struct Impl {
   static void residual_restrict(mg_handle* h, int l, int cur) {
     LevelBuf& Lv = h->lv[l];
     LevelBuf& Cv = h->lv[l + 1];
-    if (Lv.zs) {
-      zs_launch(h, l, PolResid<TV, TV, TC>{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)}, MG_K_RESID);
-    } else if (Lv.tma) {
+    if (Lv.tma) {
       tma_launch<TK_RESID, false, false>(h, l, Lv.m_full_x[cur], nullptr, V(Lv.r), nullptr, 0.0, 0.0, 0.0,
                                          MG_K_RESID);
     } else if (Lv.g27) {
@@ -1172,19 +1118,16 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
     const LevelBuf& L0 = h->lv[0];
     k_diag64<<<lin_blocks(h, L0.g.npts()), 256, 0, h->s>>>(L0.kx64, L0.ky64, L0.kz64, h->dg64, L0.g);
     CKL();
+    if (p.test_inject == 1) {  // test only: an indefinite outer operator (p.Ap < 0)
+      k_scale_strided<<<lin_blocks(h, n0), 256, 0, h->s>>>(h->dg64, -1.0, n0, 1);
+      CKL();
+    }
   }
   if (!mixed) h->lv[0].b = h->cr;  // the V-cycle's finest right-hand side is the CG residual
   // TMA-staged stencil kernels on the levels above the bottom kernel
   for (int l = 0; l < h->lb; ++l) {
     if (h->lv[l].g27) continue;  // the staged kernels read 7-point edge coefficients
-    if (p.stencil_kernel == 1 || p.stencil_kernel == 3) {
-      dispatch(h, [&](auto impl) {
-        decltype(impl)::zs_prepare(h, l);
-        return 0;
-      });
-      if (p.stencil_kernel == 3) h->lv[l].zs = true;
-      else h->lv[l].zs_prolong = h->lv[l].g.nx >= 64 && h->lv[l].g.ny >= 64;
-    } else if (p.stencil_kernel == 2) {
+    if (p.stencil_kernel == 1) {
       const bool ok = dispatch(h, [&](auto impl) { return decltype(impl)::tma_prepare(h, l); });
       if (!ok) return fail(h, MG_ERR_CUDA, "TMA tensor map encoding failed");
     }
@@ -1205,10 +1148,6 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   if (h->lv[0].tma) {
     const int tg = h->lv[0].tma_grid[0] * h->lv[0].tma_grid[1] * h->lv[0].tma_grid[2];
     if (h->pstride < tg) h->pstride = tg;
-  }
-  if (h->lv[0].zs || h->lv[0].zs_prolong) {
-    const int zg = h->lv[0].zs_grid[0] * h->lv[0].zs_grid[1] * h->lv[0].zs_grid[2];
-    if (h->pstride < zg) h->pstride = zg;
   }
   AL(h->partials, double, 2 * (i64)h->pstride);
   AL(h->dsc, Scal, 1);
@@ -1237,6 +1176,10 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
     AL(h->Ac, double, (i64)h->nc * h->nc);
     CK(cudaMemcpyAsync(h->Ac, h->Lc, sizeof(double) * h->nc * h->nc, cudaMemcpyDeviceToDevice, h->s));
   }
+  if (p.test_inject == 2) {  // test only: a coarsest operator that is not positive definite
+    k_scale_strided<<<1, 256, 0, h->s>>>(h->Lc, -1.0, (i64)h->nc, (i64)h->nc + 1);
+    CKL();
+  }
   CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s));
   k_cholesky<<<1, 1024, 0, h->s>>>(h->Lc, h->nc, h->dflag);
   CKL();
@@ -1258,6 +1201,9 @@ void release(mg_handle* h) {
   if (h->s) cudaStreamSynchronize(h->s);
   for (void* p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  for (auto& pr : h->gap_ev)
+    for (cudaEvent_t e : pr)
+      if (e) cudaEventDestroy(e);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->s) cudaStreamDestroy(h->s);
@@ -1269,8 +1215,12 @@ void release(mg_handle* h) {
 
 // Runs the V-cycle (and, in mixed precision, the casts around it); through a
 // CUDA graph captured on first use when the handle enables graphs.
+// kernel classes launched inside the V-cycle (and its graph)
+constexpr int VCYCLE_CLASSES = (1 << MG_K_CHEB_ZERO) | (1 << MG_K_CHEB_STEP) | (1 << MG_K_RESID) |
+                               (1 << MG_K_RESTRICT) | (1 << MG_K_PROLONG) | (1 << MG_K_BOTTOM) | (1 << MG_K_DOT);
+
 template <class I, class TV> mg_status run_precondition(mg_handle* h, TV** z) {
-  if (!h->prm.use_graph || h->timing) {  // timed launches run eagerly: plain stream events
+  if (!h->prm.use_graph || (h->timing && (h->t_cls_mask & VCYCLE_CLASSES))) {  // timed launches run eagerly
     *z = I::precondition(h);
     CKL();
     return MG_OK;
@@ -1373,17 +1323,29 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
     TV* z = nullptr;
     I::cast_rhs(h);
     if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
+    const bool gap_on = h->timing && ((h->t_cls_mask >> MG_K_HOST_GAP) & 1) && h->gap_ev[0][0];
+    int gap_prev = -1;  // event pair recorded in the previous iteration, read after the next host sync
     for (it = 1; it <= p.maxit; ++it) {
       if (p.flexible) cg_iteration<I, true>(h, z, g, L0);
       else cg_iteration<I, false>(h, z, g, L0);
+      const int gp = it & 1;
+      if (gap_on) CK(cudaEventRecord(h->gap_ev[gp][0], h->s));
       if ((s = read_scal(h)) != MG_OK) return s;
+      if (gap_prev >= 0) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->gap_ev[gap_prev][0], h->gap_ev[gap_prev][1]));
+        h->t_ms[MG_K_HOST_GAP][0] += ms;
+        h->t_n[MG_K_HOST_GAP][0] += 1;
+        gap_prev = -1;
+      }
       sc = *h->hsc;
-      if (sc.status & 1) {
-        result = fail(h, MG_ERR_NONFINITE, "non-finite value during the iteration");
+      if (sc.status & ST_TIMEOUT) {  // checked first: the blocks that gave up left their outputs unwritten
+        result = fail(h, MG_ERR_DEVICE_TIMEOUT,
+                      "a bounded wait in a TMA-staged kernel gave up; the iterate is invalid");
         break;
       }
-      if (sc.status & ST_TIMEOUT) {
-        result = fail(h, MG_ERR_DEVICE_TIMEOUT, "a bounded wait in a TMA-staged kernel gave up");
+      if (sc.status & 1) {
+        result = fail(h, MG_ERR_NONFINITE, "non-finite value during the iteration");
         break;
       }
       if (sc.status & 2) {
@@ -1396,6 +1358,10 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
       if (it == p.maxit) {
         result = fail(h, MG_ERR_NOT_CONVERGED, "maximum number of iterations reached");
         break;
+      }
+      if (gap_on) {
+        CK(cudaEventRecord(h->gap_ev[gp][1], h->s));
+        gap_prev = gp;
       }
       if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
     }
@@ -1646,6 +1612,7 @@ mg_status mg_params_default(mg_params* p) {
   p->coarse_rtol = 1e-4;
   p->coarse_maxit = 30;
   p->bottom_blocks = 0;
+  p->test_inject = 0;
   return MG_OK;
 }
 
@@ -1661,12 +1628,13 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   if (p.nu_pre < 0 || p.nu_post < 0 || p.cheby_degree < 1 || p.cheby_degree > BOT_MAXDEG || p.maxit < 0 || !(p.eig_hi > 0) ||
       !(p.eig_lo_frac > 0 && p.eig_lo_frac < 1) || p.coarse_k_rule < 0 || p.coarse_k_rule > 2 || p.face_rule < 0 ||
       p.face_rule > 1 || p.precision < MG_FP64 || p.precision > MG_MIXED_BF16K || p.levels < 0 ||
-      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 4 ||
+      p.levels > MG_MAX_LEVELS || p.stencil_kernel < 0 || p.stencil_kernel > 2 ||
       p.smoother < MG_SMOOTHER_CHEBYSHEV || p.smoother > MG_SMOOTHER_RICHARDSON || !(p.richardson_omega > 0.0) ||
       p.coarse_op < MG_COARSE_REDISCRETISED || p.coarse_op > MG_COARSE_GALERKIN || p.krylov < MG_KRYLOV_CG ||
       p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256 || p.eig_mode < 0 ||
       p.eig_mode > 1 || !(p.eig_safety > 0.0) || p.coarse_solve < 0 || p.coarse_solve > 1 ||
-      !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32 || (p.bottom_blocks != 0 && p.bottom_blocks != 1 && p.bottom_blocks != 2 && p.bottom_blocks != 4 && p.bottom_blocks != 8))
+      !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32 || (p.bottom_blocks != 0 && p.bottom_blocks != 1 && p.bottom_blocks != 2 && p.bottom_blocks != 4 && p.bottom_blocks != 8) ||
+      p.test_inject < 0 || p.test_inject > 3)
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible
@@ -1677,7 +1645,7 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   mg_handle* h = new (std::nothrow) mg_handle();
   if (!h) return fail(nullptr, MG_ERR_ALLOC, "host allocation failed");
   h->prm = p;
-  h->zvec = p.stencil_kernel != 4;
+  h->zvec = p.stencil_kernel != 2;
   h->us = (cudaStream_t)stream;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1720,6 +1688,33 @@ mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_sta
   if (h->prm.krylov == MG_KRYLOV_FGMRES)
     return dispatch(h, [&](auto impl) { return fgmres_impl<decltype(impl)>(h, f, x, rtol, st); });
   return dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, f, x, rtol, st); });
+}
+
+mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, double rtol, mg_stats* st) {
+  if (!h || !f_host || !x_host || !(rtol >= 0))
+    return h ? fail(h, MG_ERR_ARG, "null pointer or negative rtol") : MG_ERR_ARG;
+  auto t0 = clk::now();
+  const LevelBuf& L0 = h->lv[0];
+  const size_t bytes = sizeof(double) * (size_t)L0.N[0] * L0.N[1] * L0.N[2];
+  Guard guard(h);
+  if (!h->hstage[0]) {
+    for (double*& b : h->hstage) AL(b, double, (i64)(bytes / sizeof(double)));
+  }
+  CK(cudaMemcpyAsync(h->hstage[0], f_host, bytes, cudaMemcpyHostToDevice, h->s));
+  if (h->prm.nonzero_guess) CK(cudaMemcpyAsync(h->hstage[1], x_host, bytes, cudaMemcpyHostToDevice, h->s));
+  mg_status s;
+  if (h->prm.krylov == MG_KRYLOV_FGMRES)
+    s = dispatch(h, [&](auto impl) { return fgmres_impl<decltype(impl)>(h, h->hstage[0], h->hstage[1], rtol, st); });
+  else
+    s = dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, h->hstage[0], h->hstage[1], rtol, st); });
+  if (s != MG_OK && s != MG_ERR_NOT_CONVERGED && s != MG_ERR_BREAKDOWN && s != MG_ERR_NONFINITE &&
+      s != MG_ERR_DEVICE_TIMEOUT)
+    return s;
+  CK(cudaMemcpyAsync(x_host, h->hstage[1], bytes, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  h->st.solve_s = secs(t0);  // the whole call, copies included
+  if (st) *st = h->st;
+  return s;
 }
 
 mg_status mg_gradient(mg_handle* h, const double* phi, const double* lambda, double* grad) {
@@ -1995,6 +1990,8 @@ mg_status mg_timing_enable(mg_handle* h, int class_mask, int level_mask) {
   if (on && h->evpool.empty()) {
     h->evpool.resize(EV_POOL);
     for (auto& e : h->evpool) CK(cudaEventCreate(&e));
+    for (auto& pr : h->gap_ev)
+      for (cudaEvent_t& e : pr) CK(cudaEventCreate(&e));
   }
   if (h->vexec) {
     cudaGraphExecDestroy(h->vexec);

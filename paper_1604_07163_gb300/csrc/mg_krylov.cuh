@@ -63,6 +63,13 @@ __global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src
     dst[t] = src[t] * s;
 }
 
+// a[t * stride] *= s for t < n, in place: the host-requested data
+// perturbations that exercise the error paths (mg_params.test_inject)
+__global__ void k_scale_strided(double* a, double s, i64 n, i64 stride) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    a[t * stride] *= s;
+}
+
 // y = A u in float64 for an operand u stored in the V-cycle precision TZ
 template <class TZ> struct OpApplyTo64 {
   using Real = double;

@@ -11,8 +11,15 @@
 // Completion is tracked with one mbarrier per stage (expected transaction
 // bytes).  Planes k-1, k, k+1 of the stencil vector are resident while plane
 // k is computed, and the copies of plane k+2 are in flight.  Every wait on an
-// mbarrier is bounded; a block that gives up sets bit 2 of the status word,
-// waits (bounded) for the copies it issued, and returns.
+// mbarrier is bounded (poll_limit polls); a block whose wait gives up sets bit
+// ST_TIMEOUT of the status word, then waits, with the full TMA_POLL_LIMIT, for
+// every copy it has issued whose completion it has not yet seen (the stage
+// whose wait gave up included), and returns without writing the rest of its
+// outputs.  After ST_TIMEOUT the host must treat the whole solve, and every
+// kernel that ran after this one on the stream, as invalid; mg_solve then
+// returns MG_ERR_DEVICE_TIMEOUT.  (Should the drain itself give up, copies
+// could still land in the shared memory of a block that the SM schedules
+// next: one more reason to discard everything after the flag.)
 //
 // Arrays are viewed as 2-D tensors of rows of Px elements (the padded layout
 // of mg_device.cuh puts interior row j of plane k at row
@@ -29,6 +36,7 @@ namespace mgdev {
 
 constexpr int TT_X = 32, TT_Y = 8, TT_THREADS = 256, TT_NS = 4;
 constexpr int ST_TIMEOUT = 4;  // status bit set by a bounded wait that gave up
+constexpr int TMA_POLL_LIMIT = 1 << 20;  // polls of one bounded wait (each may suspend briefly)
 
 enum TmaKind { TK_STEP = 0, TK_ZERO = 1, TK_RESID = 2 };
 
@@ -57,10 +65,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after a fixed number of polls (each poll may suspend
-// the thread for a short hardware-defined time).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it)
+// Bounded wait: gives up after limit polls (each poll may suspend the thread
+// for a short hardware-defined time; limit 0 gives up at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -117,6 +125,7 @@ template <class TV, class TC> struct TmaArgs {
   double dc1, dc2, dinv_theta;
   double* partials;  // DOT: per-block sums of r.z
   int* status;       // bit ST_TIMEOUT on a wait that gave up
+  int poll_limit;    // polls of each wait in the main loop (TMA_POLL_LIMIT; 0 only to test the give-up path)
 };
 
 template <int KIND, bool HAS_D, bool DOT, class TV, class TC>
@@ -172,12 +181,16 @@ __global__ void __launch_bounds__(TT_THREADS) k_tma_stencil(const __grid_constan
 
   double acc = 0.0, acc1 = 0.0;
   bool bad = false;
-  int waited = -1;  // highest sequence number waited for
+  int done = -1;  // every sequence number <= done has been seen complete by this thread
   for (int k = k0; k < k1; ++k) {
     const int n = k - k0 + 1;
-    for (int m = waited + 1; m <= n + 1; ++m)
-      if (!mbar_wait_bounded(&full[m % TT_NS], (unsigned)((m / TT_NS) & 1))) bad = true;
-    waited = n + 1;
+    for (int m = done + 1; m <= n + 1; ++m) {
+      if (!mbar_wait_bounded(&full[m % TT_NS], (unsigned)((m / TT_NS) & 1), a.poll_limit)) {
+        bad = true;
+        break;
+      }
+      done = m;
+    }
     if (__syncthreads_or(bad)) {  // every thread leaves together
       bad = true;
       break;
@@ -248,9 +261,13 @@ __global__ void __launch_bounds__(TT_THREADS) k_tma_stencil(const __grid_constan
   }
   pdl_trigger();
   if (bad) {
+    // thread 0 issued every copy; stages reuse only after all threads passed
+    // their waits, so each sequence number in (done, issued) is the pending
+    // phase of its stage
     if (tid == 0) {
       atomicOr(a.status, ST_TIMEOUT);
-      for (int m = waited + 1; m < issued; ++m) mbar_wait_bounded(&full[m % TT_NS], (unsigned)((m / TT_NS) & 1));
+      for (int m = done + 1; m < issued; ++m)
+        mbar_wait_bounded(&full[m % TT_NS], (unsigned)((m / TT_NS) & 1), TMA_POLL_LIMIT);
     }
     return;
   }

@@ -44,6 +44,7 @@ class Params:
     coarse_rtol: float = 1e-4
     coarse_maxit: int = 30
     bottom_blocks: int = 0  # 0 automatic; 1 one block; 2, 4, 8 a thread-block cluster
+    test_inject: int = 0  # test only: 1 negated outer diagonal (breakdown), 2 negated coarsest diagonal (not SPD)
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -62,6 +63,7 @@ class Params:
         p.coarse_rtol = self.coarse_rtol
         p.coarse_maxit = self.coarse_maxit
         p.bottom_blocks = self.bottom_blocks
+        p.test_inject = self.test_inject
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p
@@ -177,15 +179,35 @@ class MGSolver:
 
     # -------------------------------------------------------------- solves
     def solve(self, f: torch.Tensor, rtol: float, x: torch.Tensor | None = None, raise_on_error: bool = True):
-        """Return (x, Stats) for A x = f."""
+        """Return (x, Stats) for A x = f.  With raise_on_error=False the
+        outcomes of the iteration itself (not converged, breakdown, a
+        non-finite value, a device wait that gave up) come back in
+        Stats.status instead of raising; argument, allocation and CUDA errors
+        always raise."""
         f = self._nodal(f)
         x = self._new() if x is None else self._nodal(x)
         st = L.MgStats()
         self._sync_stream()
         rc = self._lib.mg_solve(self._h, _ptr(f), _ptr(x), float(rtol), C.byref(st))
-        if rc != L.MG_OK and (raise_on_error or rc not in (5,)):
+        if rc != L.MG_OK and (raise_on_error or rc not in L.SOLVE_OUTCOMES):
             self._check(rc)
         return x, self._stats(st, rc)
+
+    def solve_host(self, f: torch.Tensor, x: torch.Tensor, rtol: float, raise_on_error: bool = True) -> Stats:
+        """Solve A x = f with f and x in HOST memory (float64 CPU tensors of the
+        grid's shape; pinned memory gives full-bandwidth copies): the library
+        copies f in and x out inside the call.  Returns the Stats; x is
+        overwritten with the solution."""
+        for t in (f, x):
+            if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.float64
+                    and tuple(t.shape) == self.shape and t.is_contiguous()):
+                raise ValueError(f"expected a contiguous float64 CPU tensor of shape {self.shape}")
+        st = L.MgStats()
+        self._sync_stream()
+        rc = self._lib.mg_solve_host(self._h, _ptr(f), _ptr(x), float(rtol), C.byref(st))
+        if rc != L.MG_OK and (raise_on_error or rc not in L.SOLVE_OUTCOMES):
+            self._check(rc)
+        return self._stats(st, rc)
 
     def solve_adjoint(self, g: torch.Tensor, rtol: float, phi: torch.Tensor | None = None, want_grad: bool = True):
         """Return (lambda, grad_logk or None, Stats) for A lambda = g."""
@@ -310,8 +332,9 @@ class MGSolveFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gphi):
         (phi,) = ctx.saved_tensors
+        # the solver stays open until ctx is collected (MGSolver.__del__ frees
+        # it), so a second backward through the same graph works too
         lam, grad, _ = ctx.solver.solve_adjoint(gphi.contiguous(), ctx.rtol, phi, want_grad=ctx.needs_input_grad[1])
-        ctx.solver.close()
         return lam, grad, None, None
 
 

@@ -52,8 +52,8 @@ def test_params_struct_layout_and_defaults(lib):
     assert p.precision == 0 and p.face_rule == 0 and p.coarse_k_rule == 0 and p.flexible == -1
     assert (p.stencil_kernel, p.use_pdl, p.smoother, p.richardson_omega, p.coarse_op, p.krylov,
             p.gmres_restart, p.eig_mode, p.eig_safety,
-            p.coarse_solve, p.coarse_rtol, p.coarse_maxit, p.bottom_blocks) == (
-                0, 1, 0, 6.0 / 7.0, 0, 0, 30, 0, 1.1, 0, 1e-4, 30, 0)
+            p.coarse_solve, p.coarse_rtol, p.coarse_maxit, p.bottom_blocks, p.test_inject) == (
+                0, 1, 0, 6.0 / 7.0, 0, 0, 30, 0, 1.1, 0, 1e-4, 30, 0, 0)
     assert lib.mg_params_default(None) == 1
 
 
@@ -69,9 +69,13 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
         assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
         assert b"mg_params" in lib.mg_last_error(None)
     p.cheby_degree = 2
-    p.stencil_kernel = 5  # kernels 0..4
+    p.stencil_kernel = 3  # kernels 0..2
     assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
     p.stencil_kernel = 0
+    for bad in (-1, 4):  # test_inject 0..3
+        p.test_inject = bad
+        assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1
+    p.test_inject = 0
     for smoother, omega in ((2, 1.0), (1, 0.0), (1, -0.5)):
         p.smoother, p.richardson_omega = smoother, omega
         assert lib.mg_setup(ctypes.byref(h), 9, 9, 9, ctypes.c_void_p(1), 1, ctypes.byref(p), None) == 1

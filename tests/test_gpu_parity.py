@@ -73,13 +73,11 @@ def make(dims, block, rng, params, seed=101):
     return k, O, S
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_step_parity_fp64(gpu_lib, case, kernel):
-    """kernel 0: default z-marching with two points per thread; 1: plus
-    prolongation folded into the first post-smoothing step on large levels;
-    2: TMA-staged tiles; 3: shared-plane z-marching for every pass;
-    4: z-marching with one point per thread."""
+    """kernel 0: default z-marching with two points per thread; 1: TMA-staged
+    tiles; 2: z-marching with one point per thread."""
     dims, block, rng, params = CASES[case]
     k, O, S = make(dims, block, rng, dict(params, stencil_kernel=kernel))
     for l in range(O.levels):
@@ -103,11 +101,11 @@ def test_step_parity_fp64(gpu_lib, case, kernel):
     assert relmax(N(S.apply(T(x), -1)), O.apply(x)) < 1e-13
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_vcycle_parity_large_levels(gpu_lib, kernel):
-    """129^3: levels with >= 64 points per axis, where kernel 1 folds the
-    coarse-grid correction into the first post-smoothing step; also the
-    float32 V-cycle of the same hierarchy."""
+    """129^3: levels large enough for several tiles and plane chunks per
+    block under every kernel choice; also the float32 V-cycle of the same
+    hierarchy."""
     import paper_1604_07163_gb300 as mg
     dims = (129, 129, 129)
     k = mi.cell_k(dims, 8, -2.0, 2.0, 55)
@@ -141,16 +139,15 @@ def test_gradient_kernel_parity(gpu_lib):
         assert relmax(N(S.gradient(T(phi), T(lam))), O.gradient(phi, lam)) < 1e-13
 
 
-@pytest.mark.parametrize("name,n,tol,dit", [("poisson33_fp64", None, 1e-10, 1), ("adjoint129", None, 1e-10, 1),
-                                            ("poisson257_c1e4", 65, 2e-9, 2)])
-def test_solve_parity_fp64(gpu_lib, name, n, tol, dit):
+@pytest.mark.parametrize("name,n", [("poisson33_fp64", None), ("adjoint129", None), ("poisson257_c1e4", 65)])
+def test_solve_parity_fp64(gpu_lib, name, n):
     """The two FP64 runs differ only in rounding order (tree vs sequential dot
-    products, fused multiply-adds).  CG amplifies that difference with the
-    condition number: at 10^2 contrast (33^3, 129^3) the solutions agree to
-    1e-10 and the iteration counts to 1; at 10^4 contrast the amplification
-    reaches a few 1e-10 after ~35 iterations and the residual history is flat
-    near the tolerance (a ratio of ~0.7 per iteration), so that case is held to
-    2e-9 (a fifth of its solve tolerance) and iteration counts within 2."""
+    products, fused multiply-adds): the solution agrees to relative 1e-10 in
+    the 2-norm and the iteration count to within 1 (the spec bar), also
+    at 10^4 contrast, where the oracle run against itself with its second
+    summation order moves by 2e-10 and one iteration
+    (tests/golden/oracle_spread.json)."""
+    tol, dit = 1e-10, 1
     dims, k, f, spec = mi.workload(name, n)
     O = oracle.Oracle(k)
     xo, ito, info = O.pcg(f, spec["rtol"], maxit=2000)
@@ -168,7 +165,7 @@ def test_solve_parity_fp64(gpu_lib, name, n, tol, dit):
     # recurrence-residual history agrees iteration by iteration (at high contrast
     # only over the first iterations, before rounding differences have grown)
     h = np.array(st.history)
-    m = min(len(h), len(info["hist"]), len(h) if tol <= 1e-10 else 10)
+    m = min(len(h), len(info["hist"]), len(h) if name != "poisson257_c1e4" else 10)
     assert np.max(np.abs(h[:m] - info["hist"][:m]) / info["hist"][:m]) < 1e-6
 
 
@@ -192,8 +189,9 @@ def test_solve_parity_paper_smoothers(gpu_lib, params, dit):
 @pytest.mark.parametrize("precision", ["fp64", "mixed_fp32", "mixed_bf16k"])
 def test_galerkin_solve_parity_high_contrast(gpu_lib, precision):
     """Galerkin coarse operators at k contrast 10^6 (log10 k ~ U[-3,3]): the
-    float64 form takes the oracle's iteration count (within 2: CG amplifies
-    rounding differences at this contrast) and solution; the mixed forms reach
+    float64 form takes the oracle's iteration count (within 1) and solution
+    (relative 1e-10; the oracle's own two summation orders agree to 6e-16
+    here, tests/golden/oracle_spread.json); the mixed forms reach
     the tolerance on the oracle's own operator (with a float32 V-cycle at this
     contrast CG needs up to ~25% more iterations: measured 75 against 62)."""
     import paper_1604_07163_gb300 as mg
@@ -205,8 +203,8 @@ def test_galerkin_solve_parity_high_contrast(gpu_lib, precision):
     x, st = mg.MGSolver(T(k), mg.Params(maxit=400, coarse_op="galerkin", precision=precision)).solve(T(f), 1e-10)
     xn = N(x)
     if precision == "fp64":
-        assert abs(st.iters - ito) <= 2
-        assert rel2(xn, xo) < 2e-9
+        assert abs(st.iters - ito) <= 1
+        assert rel2(xn, xo) < 1e-10
     else:
         true = np.linalg.norm((f - O.apply(xn))[1:-1, 1:-1, 1:-1]) / np.linalg.norm(f)
         assert true <= 1.01e-10
@@ -294,8 +292,8 @@ def test_telescoping_graph_and_kernel_choice_do_not_change_the_result(gpu_lib):
     import paper_1604_07163_gb300 as mg
     dims, k, f, spec = mi.workload("poisson33_fp64", 65)
     ref = None
-    for tele, graph, kern, pdl in [(0, 0, 1, 0), (4096, 1, 0, 1), (40000, 1, 2, 1), (10 ** 6, 0, 0, 1),
-                                   (4096, 1, 2, 0), (4096, 1, 3, 1), (4096, 1, 4, 1)]:
+    for tele, graph, kern, pdl in [(0, 0, 1, 0), (4096, 1, 0, 1), (40000, 1, 1, 1), (10 ** 6, 0, 0, 1),
+                                   (4096, 1, 1, 0), (4096, 1, 2, 1), (0, 1, 2, 0)]:
         x, st = mg.MGSolver(T(k), mg.Params(telescope_max_n=tele, use_graph=graph, stencil_kernel=kern,
                                             use_pdl=pdl)).solve(T(f), 1e-10)
         if ref is None:
@@ -346,7 +344,7 @@ def test_mixed_precision_reaches_fp64_tolerance(gpu_lib, precision):
     assert st.iters <= ito + 6
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("precision,tol", [("mixed_fp32", 2e-6), ("mixed_bf16k", 2e-2)])
 def test_mixed_step_parity(gpu_lib, precision, tol, kernel):
     """float32 vectors: rounding of order 1e-7 relative per step; bfloat16
@@ -395,6 +393,49 @@ def test_nonfinite_and_invalid_inputs(gpu_lib):
     with pytest.raises(mg.MgError) as e:
         mg.MGSolver(T(np.ones((32, 32, 32))), mg.Params(levels=1))  # 31^3 unknowns > dense limit
     assert e.value.status == "MG_ERR_ARG"
+
+
+def test_injected_breakdown_and_not_spd(gpu_lib):
+    """Error paths made by host-side data perturbations (mg_params.test_inject),
+    no GPU fault: a negated outer diagonal makes p.Ap < 0, which the device
+    reduction flags and mg_solve reports as MG_ERR_BREAKDOWN after one
+    iteration; a negated coarsest diagonal makes the Cholesky factorisation
+    meet a non-positive pivot, which mg_setup reports as MG_ERR_NOT_SPD.  A
+    clean handle built afterwards solves normally."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    for prec in ("fp64", "mixed_fp32"):
+        S = mg.MGSolver(T(k), mg.Params(precision=prec, test_inject=1))
+        x, st = S.solve(T(f), 1e-10, raise_on_error=False)
+        assert st.status == "MG_ERR_BREAKDOWN" and st.iters == 1, (prec, st.status, st.iters)
+        with pytest.raises(mg.MgError) as e:
+            S.solve(T(f), 1e-10)
+        assert e.value.status == "MG_ERR_BREAKDOWN"
+        S.close()
+        with pytest.raises(mg.MgError) as e:
+            mg.MGSolver(T(k), mg.Params(precision=prec, test_inject=2))
+        assert e.value.status == "MG_ERR_NOT_SPD"
+    x, st = mg.MGSolver(T(k)).solve(T(f), 1e-10)
+    assert st.status == "MG_OK" and st.true_rel_resid <= 1.01e-10
+
+
+def test_tma_wait_give_up_returns_device_timeout(gpu_lib):
+    """The TMA-staged kernels' bounded waits, made to give up at once
+    (test_inject 3: no polling in the main loop): every block flags the
+    timeout, drains the copies it issued with the full poll limit and
+    returns; mg_solve reports MG_ERR_DEVICE_TIMEOUT (the iterate is invalid)
+    and the context stays usable: the same solve with the ordinary limit
+    matches the oracle."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64", 65)
+    for prec in ("fp64", "mixed_fp32"):
+        S = mg.MGSolver(T(k), mg.Params(precision=prec, stencil_kernel=1, test_inject=3))
+        x, st = S.solve(T(f), 1e-10, raise_on_error=False)
+        assert st.status == "MG_ERR_DEVICE_TIMEOUT", (prec, st.status)
+        S.close()
+    xo, ito, _ = oracle.Oracle(k).pcg(f, 1e-10)
+    x, st = mg.MGSolver(T(k), mg.Params(stencil_kernel=1)).solve(T(f), 1e-10)
+    assert abs(st.iters - ito) <= 1 and rel2(N(x), xo) < 1e-10
 
 
 def test_single_level_is_a_direct_solve(gpu_lib):
@@ -452,6 +493,27 @@ def test_nonzero_initial_guess(gpu_lib):
     assert st2.iters == 0
 
 
+def test_solve_with_host_buffers_matches_the_device_solve(gpu_lib):
+    """mg_solve_host copies a host f in and x out inside the call: with pinned
+    or pageable host memory it returns the device solve's iterate bit for bit,
+    and with nonzero_guess it reads the host x as the initial guess."""
+    import paper_1604_07163_gb300 as mg
+    dims, k, f, spec = mi.workload("poisson33_fp64")
+    S = mg.MGSolver(T(k))
+    xd, st = S.solve(T(f), 1e-10)
+    for pinned in (True, False):
+        fh = torch.tensor(f)
+        xh = torch.zeros(dims, dtype=torch.float64)
+        if pinned:
+            fh, xh = fh.pin_memory(), xh.pin_memory()
+        sth = S.solve_host(fh, xh, 1e-10)
+        assert sth.iters == st.iters and sth.status == "MG_OK"
+        assert torch.equal(xh, xd.cpu())
+    Sg = mg.MGSolver(T(k), mg.Params(nonzero_guess=1))
+    xh = xd.cpu().clone()
+    assert Sg.solve_host(torch.tensor(f), xh, 1e-8).iters == 0
+
+
 def test_residual_norm_entry_point(gpu_lib):
     import paper_1604_07163_gb300 as mg
     dims, k, f, spec = mi.workload("poisson33_fp64")
@@ -482,10 +544,15 @@ def test_adjoint_gradient_parity_129(gpu_lib):
     ft = T(f).requires_grad_(True)
     phi = mg.mg_solve(ft, logk, rtol=1e-12)
     loss = 0.5 * ((phi - T(phi_obs)) ** 2 * T(mask.astype(np.float64))).sum()
-    loss.backward()
+    loss.backward(retain_graph=True)
     assert rel2(N(phi), phi_o) < 1e-10
     assert rel2(N(ft.grad), lam_o) < 1e-9
     assert rel2(N(logk.grad), grad_o) < 1e-8
+    # a second backward through the same graph reuses the forward's solver
+    g1 = logk.grad.clone()
+    logk.grad = None
+    loss.backward()
+    assert torch.equal(logk.grad, g1)
 
 
 @pytest.mark.parametrize("params", [dict(coarse_op="galerkin"),
@@ -532,30 +599,53 @@ def test_fgmres_nonzero_initial_guess(gpu_lib):
 
 
 def test_gradient_finite_differences_gpu(gpu_lib):
-    """Central differences (h = 1e-6, forward solves to 1e-13) on 32 seeded cells."""
+    """The adjoint workload as its configuration states it: 129^3 vertices,
+    loss 0.5 sum over a seeded 5% node mask of (phi - phi_obs)^2, central
+    differences with h = 1e-6 on 32 seeded random cells (and on the 32 cells
+    of largest gradient), forward solves to 1e-13.
+
+    A difference quotient cannot resolve a change of L smaller than a few
+    units in the last place of L: with L ~ 6e-5, ten ulps over 2h is about
+    7e-14, against per-cell gradients of 1e-11 .. 1e-8 here.  Each cell must
+    agree within 1e-3 relative plus that floor, the median over the random
+    cells within 1e-3, and the largest-gradient cells (well above the floor)
+    within 1e-5 relative.  (Measured on GB300: median 1.3e-4, largest
+    absolute error 1.1e-14; largest-gradient cells within 2.1e-6.)"""
     import paper_1604_07163_gb300 as mg
-    dims, k, f, spec = mi.workload("adjoint129", 33)
+    dims, k, f, spec = mi.workload("adjoint129")
     kobs = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], spec["seed"] + 1)
     phi_obs = T(oracle.Oracle(kobs).pcg(f, 1e-13)[0])
-    mask = T(mi.obs_mask(dims, spec["seed"], frac=0.2).astype(np.float64))
+    mask = T(mi.obs_mask(dims, spec["seed"]).astype(np.float64))
     ft = T(f)
     lk = np.log(k)
 
-    def loss(lkv, grad=False):
-        logk = T(lkv).requires_grad_(grad)
-        phi = mg.mg_solve(ft, logk, rtol=1e-13)
-        Lv = 0.5 * ((phi - phi_obs) ** 2 * mask).sum()
-        if grad:
-            Lv.backward()
-            return Lv.item(), N(logk.grad)
-        return Lv.item()
+    def loss(lkv):
+        S = mg.MGSolver(T(lkv), k_is_log=True)
+        phi, st = S.solve(ft, 1e-13)
+        S.close()
+        return 0.5 * ((phi - phi_obs) ** 2 * mask).sum().item()
 
-    L0, g = loss(lk, True)
-    rng = np.random.default_rng(5)
-    cells = [tuple(c) for c in rng.integers(0, 32, (32, 3))]
+    logk = T(lk).requires_grad_(True)
+    phi = mg.mg_solve(ft, logk, rtol=1e-13)
+    L0t = 0.5 * ((phi - phi_obs) ** 2 * mask).sum()
+    L0t.backward()
+    L0, g = L0t.item(), N(logk.grad)
     h = 1e-6
-    for c in cells:
+    floor = 10 * np.spacing(L0) / (2 * h)
+
+    def fd(c):
         lp = lk.copy(); lp[c] += h
         lm = lk.copy(); lm[c] -= h
-        fd = (loss(lp) - loss(lm)) / (2 * h)
-        assert abs(fd - g[c]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(g).max()), (c, fd, g[c])
+        return (loss(lp) - loss(lm)) / (2 * h)
+
+    rng = np.random.default_rng(5)
+    rel = []
+    for c in [tuple(c) for c in rng.integers(0, 128, (32, 3))]:
+        d = fd(c)
+        assert abs(d - g[c]) <= 1e-3 * abs(g[c]) + floor, (c, d, g[c], floor)
+        rel.append(abs(d - g[c]) / abs(g[c]))
+    assert np.median(rel) <= 1e-3
+    for t in np.argsort(np.abs(g).ravel())[-32:]:
+        c = np.unravel_index(t, g.shape)
+        d = fd(c)
+        assert abs(g[c]) > 1e4 * floor and abs(d - g[c]) <= 1e-5 * abs(g[c]), (c, d, g[c])
