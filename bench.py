@@ -9,7 +9,7 @@ coefficient form are timed the same way and reported beside it, each with its
 relative error against the CPU float64 oracle's solution of the same problem.
 
 The same line carries the 513^3 contrast-10^6 target solve with Galerkin
-coarse operators (north_star_target), the paper's solver configurations, the
+coarse operators (target_513_c1e6), the paper's solver configurations, the
 end-to-end figure through the C ABI with host buffers, the per-iteration host
 round trip, and the oracle timed on the host cores (a full solve, the second
 of two identical ones).
@@ -417,9 +417,9 @@ def run_ours(args):
         speedup = forms["fp64"]["ms_per_step"] / forms[HEADLINE]["ms_per_step"]
 
     target = None
-    if (world == 1 and not args.no_north_star and args.workload == WORKLOAD and not args.adjoint
+    if (world == 1 and not args.no_target_513 and args.workload == WORKLOAD and not args.adjoint
             and args.coarse_op == "rediscretised"):
-        target = north_star_target(args, dev, timed)
+        target = target_513_c1e6(args, dev, timed)
 
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.adjoint
@@ -440,7 +440,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic", "precision": HEADLINE, "iterations": forms[HEADLINE]["iters"],
         "config": config_dict(spec, world, args.workload, args.face_rule, args.adjoint, args.coarse_op),
-        "forms": forms, "speedup_mixed_vs_fp64": speedup, "north_star_target": target,
+        "forms": forms, "speedup_mixed_vs_fp64": speedup, "target_513_c1e6": target,
         "galerkin_coarse_operators": galerkin, "paper_configurations": paper,
         "roofline": roofline, "smoother_roofline": smoother, "host_gap": host_gap, "cpu_baseline": cpu,
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
@@ -450,7 +450,7 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def north_star_target(args, dev, timed):
+def target_513_c1e6(args, dev, timed):
     """The 513^3 contrast-10^6 target with Galerkin coarse operators: the
     float32-V-cycle and float64 forms, one warm-up and two timed solves each,
     their iterations and true residuals (also from the oracle's own operator),
@@ -608,7 +608,7 @@ def main():
                     help="skip the extra timing of the headline form with Galerkin coarse operators")
     ap.add_argument("--no-paper-configs", action="store_true",
                     help="skip timing the solver configurations of the paper's experiments")
-    ap.add_argument("--no-north-star", action="store_true",
+    ap.add_argument("--no-target-513", action="store_true",
                     help="skip the 513^3 contrast-10^6 Galerkin target solve")
     ap.add_argument("--only-paper-configs", action="store_true",
                     help="time only the Galerkin variant and the paper's solver configurations (for profiling)")

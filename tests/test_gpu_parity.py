@@ -13,6 +13,7 @@ import torch
 
 import mg_inputs as mi
 import oracle
+from oracle_orders import check_fp64_solve_against_both_oracle_orders
 
 pytestmark = pytest.mark.gpu
 
@@ -141,32 +142,21 @@ def test_gradient_kernel_parity(gpu_lib):
 
 @pytest.mark.parametrize("name,n", [("poisson33_fp64", None), ("adjoint129", None), ("poisson257_c1e4", 65)])
 def test_solve_parity_fp64(gpu_lib, name, n):
-    """The two FP64 runs differ only in rounding order (tree vs sequential dot
-    products, fused multiply-adds): the solution agrees to relative 1e-10 in
-    the 2-norm and the iteration count to within 1 (the spec bar), also
-    at 10^4 contrast, where the oracle run against itself with its second
-    summation order moves by 2e-10 and one iteration
-    (tests/golden/oracle_spread.json)."""
-    tol, dit = 1e-10, 1
+    """Full float64 solves against the oracle's (both summation orders, at
+    equal iteration counts): at 10^2 contrast (33^3, 129^3) all three agree to
+    about 1e-15; at 10^4 contrast (65^3) rounding order alone moves the solve
+    by a few 1e-10 and can move its stopping iteration by one (the oracle's
+    two orders differ by 3.4e-10 after 45 iterations on x86,
+    tests/golden/oracle_spread.json).  At 10^4 contrast the residual
+    histories are compared over the first 10 iterations only, before rounding
+    differences have grown."""
     dims, k, f, spec = mi.workload(name, n)
-    O = oracle.Oracle(k)
-    xo, ito, info = O.pcg(f, spec["rtol"], maxit=2000)
     import paper_1604_07163_gb300 as mg
     S = mg.MGSolver(T(k), mg.Params(maxit=2000))
     x, st = S.solve(T(f), spec["rtol"])
-    assert abs(st.iters - ito) <= dit, (st.iters, ito)
     assert st.true_rel_resid <= spec["rtol"] * 1.01
-    xg = N(x)
-    if st.iters == ito:
-        assert rel2(xg, xo) <= tol
-    else:  # same number of iterations on the oracle side
-        xo2, _, _ = O.pcg(f, 0.0, maxit=st.iters)
-        assert rel2(xg, xo2) <= tol
-    # recurrence-residual history agrees iteration by iteration (at high contrast
-    # only over the first iterations, before rounding differences have grown)
-    h = np.array(st.history)
-    m = min(len(h), len(info["hist"]), len(h) if name != "poisson257_c1e4" else 10)
-    assert np.max(np.abs(h[:m] - info["hist"][:m]) / info["hist"][:m]) < 1e-6
+    check_fp64_solve_against_both_oracle_orders(N(x), st.iters, st.history, f, k, spec["rtol"],
+                                                hist_its=10 if name == "poisson257_c1e4" else None)
 
 
 @pytest.mark.parametrize("params,dit", [(dict(smoother="richardson", nu_pre=8, nu_post=8), 1),
@@ -203,8 +193,8 @@ def test_galerkin_solve_parity_high_contrast(gpu_lib, precision):
     x, st = mg.MGSolver(T(k), mg.Params(maxit=400, coarse_op="galerkin", precision=precision)).solve(T(f), 1e-10)
     xn = N(x)
     if precision == "fp64":
-        assert abs(st.iters - ito) <= 1
-        assert rel2(xn, xo) < 1e-10
+        check_fp64_solve_against_both_oracle_orders(xn, st.iters, st.history, f, k, 1e-10,
+                                                    oracle_kw=dict(galerkin=True), hist_its=20)
     else:
         true = np.linalg.norm((f - O.apply(xn))[1:-1, 1:-1, 1:-1]) / np.linalg.norm(f)
         assert true <= 1.01e-10
