@@ -43,6 +43,7 @@ extern "C" {
 
 #define MG_MAX_LEVELS 16
 #define MG_MAX_COARSE 1024
+#define MG_MAX_SLABS 64
 
 typedef struct mg_handle mg_handle; /* opaque; owned by the library */
 
@@ -141,6 +142,21 @@ typedef struct {
                           give up without polling, so every block sets the timeout flag, drains the copies
                           it issued (with the full poll limit) and returns, and mg_solve returns
                           MG_ERR_DEVICE_TIMEOUT */
+  int slabs;           /* z-slab domain decomposition of the solve (the structured-grid decomposition of
+                          Sec. 2.2 with the coarse levels agglomerated onto one hierarchy, Sec. 3.1), 1..MG_MAX_SLABS.
+                          1 (default): none.  S > 1: every level above the agglomeration level is split into S
+                          runs of consecutive z planes (see mg_slab_plan), each slab holding its planes plus one
+                          halo plane per neighbour; every stencil and transfer pass first exchanges its
+                          operand's boundary planes with the neighbouring slabs, every dot product is summed per
+                          slab and then over the slabs in slab order, and the agglomeration level's right-hand
+                          side is gathered into the whole-grid hierarchy, whose V-cycle (bottom kernel) runs
+                          from there and whose correction is scattered back.  All slabs run on the handle's
+                          device and stream, one after another, each copy standing for a transfer between
+                          ranks.  Needs krylov = CG, stencil_kernel 0 or 2, nonzero_guess = 0.  Only mg_solve,
+                          mg_solve_host and mg_solve_adjoint use the slabs; the step entry points work on the
+                          whole grid */
+  int slab_level;      /* agglomeration level of the slabs: 0 (default) the bottom kernel's first level;
+                          otherwise that level, at most the bottom kernel's first level, at least 1 */
 } mg_params;
 
 typedef struct {
@@ -165,6 +181,17 @@ mg_status mg_params_default(mg_params* p);
  * levels, and factors the coarsest operator with a dense Cholesky. */
 mg_status mg_setup(mg_handle** h, int Nx, int Ny, int Nz, const double* k_cells, int k_on_device,
                    const mg_params* p, void* stream);
+
+/* The z-slab partition of mg_params.slabs for a grid (host arithmetic only;
+ * needs no device).  On return *agglomerate_level = la and bounds (at least
+ * (la+1)*(slabs+1) entries, cap given) holds, for every level l = 0..la and
+ * slab s, the slab's first interior z plane (0-based) at bounds[l*(slabs+1)+s],
+ * and the level's plane count at bounds[l*(slabs+1)+slabs].  On level la the
+ * planes are split as evenly as possible; on finer levels each slab owns the
+ * planes 2^(la-l) times its coarse ones (the last slab also the level's final
+ * plane), so restriction needs one halo plane above a slab and prolongation
+ * one below.  MG_ERR_ARG when the grid, the parameters or cap do not allow it. */
+mg_status mg_slab_plan(int Nx, int Ny, int Nz, const mg_params* p, int* bounds, int cap, int* agglomerate_level);
 
 /* Change the stream subsequent calls enqueue on. */
 mg_status mg_set_stream(mg_handle* h, void* stream);

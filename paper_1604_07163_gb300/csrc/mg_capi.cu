@@ -4,12 +4,15 @@
 // the float64 PCG loop and the step entry points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -50,6 +53,20 @@ struct LevelBuf {
 };
 
 std::string g_setup_error;
+
+// One step of a recorded solve phase of a z-slab sub-hierarchy (see the
+// z-slab decomposition below): a kernel launch (with the operand whose halo
+// planes it reads, if any), a memset, a reduction to finish across the slabs,
+// or the hand-over of the agglomeration level to the root hierarchy.
+struct Pass {
+  enum Kind { LAUNCH, MEMSET, FINISH, AGGLOM } kind = LAUNCH;
+  std::function<void()> fn;  // LAUNCH, MEMSET
+  void* halo = nullptr;      // LAUNCH: operand whose halo planes the kernel reads (null: pointwise)
+  int halo_bytes = 0;        // its element size
+  Geom halo_g{};             // and its level's (local) geometry
+  int nb = 0, mode = 0;      // FINISH: per-block partials and the scalar update
+  int level = 0;             // AGGLOM
+};
 
 }  // namespace
 
@@ -111,6 +128,23 @@ struct mg_handle {
   double t_ms[MG_K_NCLASS][MG_MAX_LEVELS] = {};
   long long t_n[MG_K_NCLASS][MG_MAX_LEVELS] = {};
   double t_pts[MG_K_NCLASS][MG_MAX_LEVELS] = {};
+  // z-slab decomposition (mg_params.slabs > 1).  A slab sub-hierarchy records
+  // its launches into rec instead of issuing them; halo_* name the operand of
+  // the next recorded launch; pointwise kernels of a sub-hierarchy cover its
+  // interior planes [lin_lo, lin_hi) only (its pad planes hold neighbours'
+  // halo planes).
+  std::vector<Pass>* rec = nullptr;
+  mutable void* halo_ptr = nullptr;
+  mutable int halo_bytes = 0;
+  mutable Geom halo_g{};
+  i64 lin_lo = 0, lin_hi = -1;
+  bool sub = false;                    // a slab sub-hierarchy (stream and scalars are the parent's)
+  int nslab = 1, la = 0;               // parent: slabs and agglomeration level
+  std::vector<mg_handle*> slab;        // parent: the slab sub-hierarchies
+  std::vector<int> slab_z0;            // parent: first interior plane of slab s on level l at l*(nslab+1)+s
+  double* slots = nullptr;             // parent: per-slab reduction slots (2 x nslab)
+  std::vector<std::vector<Pass>> vrec, crec;  // parent: each slab's recorded V-cycle and CG iteration
+  std::vector<void*> vz;               // parent: each slab's V-cycle output buffer
 };
 
 namespace {
@@ -136,7 +170,7 @@ void launch_cluster(const mg_handle* h, void (*kern)(KArgs...), int nb, dim3 blo
 }
 
 template <class... KArgs, class... Args>
-void launch(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+void launch_now(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -148,6 +182,27 @@ void launch(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, s
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Launch on the handle's stream; a slab sub-hierarchy in recording mode keeps
+// the launch (with its arguments and the operand named by halo_*) for replay.
+template <class... KArgs, class... Args>
+void launch(const mg_handle* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+  if (h->rec) {
+    Pass ps;
+    ps.kind = Pass::LAUNCH;
+    ps.halo = h->halo_ptr;
+    ps.halo_bytes = h->halo_bytes;
+    ps.halo_g = h->halo_g;
+    h->halo_ptr = nullptr;
+    auto tup = std::make_tuple(std::decay_t<Args>(args)...);
+    ps.fn = [h, kern, grid, block, smem, tup]() {
+      std::apply([&](const auto&... a) { launch_now(h, kern, grid, block, smem, a...); }, tup);
+    };
+    h->rec->push_back(std::move(ps));
+    return;
+  }
+  launch_now(h, kern, grid, block, smem, std::forward<Args>(args)...);
 }
 
 using clk = std::chrono::steady_clock;
@@ -340,6 +395,49 @@ dim3 zv_grid(const mg_handle* h, const Geom& g, int* kchunk) {
 // thread kernels unless the scalar driver was asked for (the float64 CG
 // operator and the 27-point operators always use the scalar driver).
 
+// The operand of a stencil or transfer pass whose z neighbours (the pad
+// planes, which hold the neighbours' planes in a z-slab) it reads; pointwise
+// passes have none.
+template <class Op> struct HaloOf {
+  static void* ptr(const Op&) { return nullptr; }
+  static int bytes() { return 0; }
+  static Geom geom(const Op&, const Geom& g) { return g; }
+};
+#define MG_HALO_OF(TPL, OPT, EXPR, TVT, GEXPR)                                \
+  template <TPL> struct HaloOf<OPT> {                                         \
+    static void* ptr(const OPT& op) { return (void*)(EXPR); }                 \
+    static int bytes() { return (int)sizeof(TVT); }                          \
+    static Geom geom(const OPT& op, const Geom& g) { return GEXPR; }          \
+  };
+#define MG_COMMA ,
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpApply<R MG_COMMA TV MG_COMMA TC>, op.u, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpChebStep<R MG_COMMA TV MG_COMMA TC>, op.x, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpChebStepDot<R MG_COMMA TV MG_COMMA TC>, op.step.x, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpChebZero<R MG_COMMA TV MG_COMMA TC>, op.b, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TB MG_COMMA class TC,
+           OpResidual<R MG_COMMA TV MG_COMMA TB MG_COMMA TC>, op.x, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV, OpRestrict<R MG_COMMA TV>, op.r, TV, op.gf)
+MG_HALO_OF(class R MG_COMMA class TV, OpProlong<R MG_COMMA TV>, op.e, TV, op.gc)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpApply27<R MG_COMMA TV MG_COMMA TC>, op.u, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpChebZero27<R MG_COMMA TV MG_COMMA TC>, op.b, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TC, OpChebStep27<R MG_COMMA TV MG_COMMA TC>, op.x, TV, g)
+MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TB MG_COMMA class TC,
+           OpResidual27<R MG_COMMA TV MG_COMMA TB MG_COMMA TC>, op.x, TV, g)
+#undef MG_HALO_OF
+#undef MG_COMMA
+template <> struct HaloOf<OpApplyPQ> {
+  static void* ptr(const OpApplyPQ& op) { return (void*)op.p; }
+  static int bytes() { return 8; }
+  static Geom geom(const OpApplyPQ&, const Geom& g) { return g; }
+};
+
+template <class Op> void set_halo(const mg_handle* h, const Op& op, const Geom& g) {
+  if (!h->rec) return;
+  h->halo_ptr = HaloOf<Op>::ptr(op);
+  h->halo_bytes = HaloOf<Op>::bytes();
+  h->halo_g = HaloOf<Op>::geom(op, g);
+}
+
 template <class R, class TV> void zv_xfer(mg_handle* h, const Geom& gc, const OpRestrict<R, TV>& op) {
   int kc;
   dim3 grid = zv_grid(h, gc, &kc);
@@ -353,6 +451,7 @@ template <class R, class TV> void zv_xfer(mg_handle* h, const Geom& g, const OpP
 template <bool RED, class Op>
 int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 0) {
   int kc;
+  set_halo(h, op, g);
   if constexpr (ZvXfer<Op>::ok) {  // prolongation / restriction: vector kernels
     if (h->zvec) {
       const int e = cls >= 0 ? tm_begin(h, cls, level) : -1;
@@ -384,6 +483,11 @@ int zmarch(mg_handle* h, const Geom& g, const Op& op, int cls = -1, int level = 
 // own resident blocks (a grid-stride loop over more blocks than fit at once
 // would leave a partial second wave).
 template <bool RED, class Op> int linear(mg_handle* h, i64 n, const Op& op, int cls = -1) {
+  i64 lo = 0;
+  if (h->lin_hi >= 0) {  // a slab: its interior planes only
+    lo = h->lin_lo;
+    n = h->lin_hi;
+  }
   static int per_sm = 0;  // per instantiation: resident blocks per SM
   if (per_sm == 0) {
     int v = 0;
@@ -391,19 +495,27 @@ template <bool RED, class Op> int linear(mg_handle* h, i64 n, const Op& op, int 
       v = 4;
     per_sm = v;
   }
-  const i64 want = (n / 4 + LIN_THREADS - 1) / LIN_THREADS;
+  const i64 want = ((n - lo) / 4 + LIN_THREADS - 1) / LIN_THREADS;
   const i64 wave = (i64)h->nsm * per_sm;
   int nb = (int)(want < wave ? want : wave);
   if (nb < 1) nb = 1;
   if (nb > h->lin_grid) nb = h->lin_grid;
   const int e = cls >= 0 ? tm_begin(h, cls, 0) : -1;
-  launch(h, k_linear<Op, RED>, dim3(nb), dim3(LIN_THREADS), 0, op, n, h->partials, h->pstride);
+  launch(h, k_linear<Op, RED>, dim3(nb), dim3(LIN_THREADS), 0, op, lo, n, h->partials, h->pstride);
   ++h->launches;
   tm_end(h, e, cls, 0, (double)h->lv[0].g.npts());
   return nb;
 }
 
 void finish(mg_handle* h, int nblocks, int mode) {
+  if (h->rec) {  // a slab: the reduction is finished across the slabs at replay
+    Pass ps;
+    ps.kind = Pass::FINISH;
+    ps.nb = nblocks;
+    ps.mode = mode;
+    h->rec->push_back(ps);
+    return;
+  }
   int flex = h->prm.flexible;
   launch(h, k_finish, dim3(1), dim3(256), 0, (const double*)h->partials, nblocks, h->pstride, mode, h->dsc, flex);
   ++h->launches;
@@ -664,6 +776,13 @@ template <class TV, class TC> struct Impl {
   }
 
   static void bottom(mg_handle* h, int l0) {
+    if (h->rec) {  // a slab reached the agglomeration level: the root takes over at replay
+      Pass ps;
+      ps.kind = Pass::AGGLOM;
+      ps.level = l0;
+      h->rec->push_back(ps);
+      return;
+    }
     BotArgs<TV, TC> a{};
     a.nlev = h->L - l0;
     for (int l = l0; l < h->L; ++l) {
@@ -735,7 +854,19 @@ template <class TV, class TC> struct Impl {
     LevelBuf& Lv = h->lv[l];
     int cur = 0;
     for (int s = 0; s < h->prm.nu_pre; ++s) cur = sweep(h, l, cur, s == 0);
-    if (h->prm.nu_pre == 0) cudaMemsetAsync(Lv.x[0], 0, (size_t)Lv.g.len * sizeof(TV), h->s);
+    if (h->prm.nu_pre == 0) {
+      void* x0 = Lv.x[0];
+      const size_t bytes = (size_t)Lv.g.len * sizeof(TV);
+      cudaStream_t st = h->s;
+      if (h->rec) {
+        Pass ps;
+        ps.kind = Pass::MEMSET;
+        ps.fn = [x0, bytes, st]() { cudaMemsetAsync(x0, 0, bytes, st); };
+        h->rec->push_back(std::move(ps));
+      } else {
+        cudaMemsetAsync(x0, 0, bytes, st);
+      }
+    }
     residual_restrict(h, l, cur);
     const int ccur = vcycle(h, l + 1);
     return correct_and_post_smooth(h, l, cur, ccur, fuse_rz);
@@ -890,8 +1021,8 @@ mg_status pack_level(mg_handle* h, int l, const double* src, void* dst, bool f64
 mg_status unpack_level(mg_handle* h, int l, const void* src, double* dst, bool f64) {
   const Geom& g = h->lv[l].g;
   const int nb = lin_blocks(h, (i64)(g.nx + 2) * (g.ny + 2) * (g.nz + 2));
-  if (f64 || h->prm.precision == MG_FP64) k_unpack<double><<<nb, 256, 0, h->s>>>((const double*)src, dst, g);
-  else k_unpack<float><<<nb, 256, 0, h->s>>>((const float*)src, dst, g);
+  if (f64 || h->prm.precision == MG_FP64) k_unpack<double><<<nb, 256, 0, h->s>>>((const double*)src, dst, g, 0, g.nz + 1);
+  else k_unpack<float><<<nb, 256, 0, h->s>>>((const float*)src, dst, g, 0, g.nz + 1);
   ++h->launches;
   CKL();
   return MG_OK;
@@ -956,10 +1087,12 @@ mg_status build_galerkin_level(mg_handle* h, int l) {
   return MG_OK;
 }
 
-mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k, int k_on_device) {
-  const mg_params& p = h->prm;
-  // level count
-  int N[3] = {Nx, Ny, Nz};
+// Level grids of the hierarchy (vertex counts per axis, level 0 finest), the
+// level count and the first level of the bottom kernel, from the grid and the
+// parameters alone (host arithmetic, no device).  Returns an error message,
+// or an empty string.
+std::string plan_hierarchy(int Nx, int Ny, int Nz, const mg_params& p, int N[MG_MAX_LEVELS][3], int* Lout,
+                           int* lbout) {
   int L = p.levels;
   if (L <= 0) {
     L = 1;
@@ -972,30 +1105,79 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
       ++L;
     }
   }
-  if (L > MG_MAX_LEVELS) return fail(h, MG_ERR_ARG, "too many levels");
+  if (L > MG_MAX_LEVELS) return "too many levels";
+  int M[3] = {Nx, Ny, Nz};
+  for (int l = 0; l < L; ++l) {
+    for (int a = 0; a < 3; ++a) {
+      if (M[a] < 3) return "level grid has fewer than 3 vertices on an axis";
+      N[l][a] = M[a];
+    }
+    if (l + 1 < L)
+      for (int a = 0; a < 3; ++a) {
+        if ((M[a] - 1) % 2) return "N-1 not divisible by 2^(levels-1)";
+        M[a] = (M[a] - 1) / 2 + 1;
+      }
+  }
+  auto npts = [&](int l) { return (i64)(N[l][0] - 2) * (N[l][1] - 2) * (N[l][2] - 2); };
+  if (make_geom(N[0][0] - 2, N[0][1] - 2, N[0][2] - 2).len >= (i64)1 << 31)
+    return "grid too large: padded arrays must stay below 2^31 elements";
+  if (npts(L - 1) > MG_MAX_COARSE) return "coarsest level exceeds MG_MAX_COARSE unknowns";
+  // telescoping: first level whose unknowns fit the bottom kernel
+  int lb = L - 1;
+  while (lb > 0 && npts(lb - 1) <= (i64)p.telescope_max_n && L - (lb - 1) <= BOT_MAX) --lb;
+  *Lout = L;
+  *lbout = lb;
+  return std::string();
+}
+
+// z-slab partition (mg_params.slabs = S > 1): the agglomeration level la
+// (slab_level, or the bottom kernel's first level, at most that) is split into
+// S runs of consecutive interior planes, slab s owning planes
+// [floor(s nz_la / S), floor((s+1) nz_la / S)); on every finer level l slab s
+// owns the planes of its coarse planes, [a 2^(la-l), b 2^(la-l)), the last slab
+// also the level's final plane (nz_l = 2 nz_{l+1} + 1).  So each slab's coarse
+// planes restrict from its own fine planes plus the first fine plane of the
+// next slab, and its fine planes prolongate from its own coarse planes plus
+// the last coarse plane of the previous slab: one halo plane per neighbour.
+// bounds[l*(S+1)+s] is slab s's first plane on level l, bounds[l*(S+1)+S] = nz_l.
+std::string plan_slabs(int Nx, int Ny, int Nz, const mg_params& p, std::vector<int>* bounds, int* laout) {
+  int N[MG_MAX_LEVELS][3], L = 0, lb = 0;
+  std::string e = plan_hierarchy(Nx, Ny, Nz, p, N, &L, &lb);
+  if (!e.empty()) return e;
+  const int S = p.slabs;
+  int la = p.slab_level > 0 ? p.slab_level : lb;
+  if (la > lb) la = lb;
+  if (la < 1) return "the slab decomposition needs at least one level above the agglomeration level";
+  const int nz_la = N[la][2] - 2;
+  if (S > nz_la) return "more slabs than interior planes on the agglomeration level";
+  bounds->assign((size_t)(la + 1) * (S + 1), 0);
+  for (int s = 0; s <= S; ++s) {
+    const int a = (int)((long long)s * nz_la / S);
+    for (int l = la; l >= 0; --l) (*bounds)[(size_t)l * (S + 1) + s] = s == S ? N[l][2] - 2 : a << (la - l);
+  }
+  *laout = la;
+  return std::string();
+}
+
+mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k, int k_on_device) {
+  const mg_params& p = h->prm;
+  int N[MG_MAX_LEVELS][3];
+  int L = 0;
+  {
+    const std::string e = plan_hierarchy(Nx, Ny, Nz, p, N, &L, &h->lb);
+    if (!e.empty()) return fail(h, MG_ERR_ARG, e);
+  }
   h->L = L;
   for (int l = 0; l < L; ++l) {
     LevelBuf& Lv = h->lv[l];
     for (int a = 0; a < 3; ++a) {
-      if (N[a] < 3) return fail(h, MG_ERR_ARG, "level grid has fewer than 3 vertices on an axis");
-      Lv.N[a] = N[a];
-      Lv.ih2[a] = (double)(N[a] - 1) * (double)(N[a] - 1);
+      Lv.N[a] = N[l][a];
+      Lv.ih2[a] = (double)(N[l][a] - 1) * (double)(N[l][a] - 1);
     }
-    Lv.g = make_geom(N[0] - 2, N[1] - 2, N[2] - 2);
-    if (l + 1 < L)
-      for (int a = 0; a < 3; ++a) {
-        if ((N[a] - 1) % 2) return fail(h, MG_ERR_ARG, "N-1 not divisible by 2^(levels-1)");
-        N[a] = (N[a] - 1) / 2 + 1;
-      }
+    Lv.g = make_geom(N[l][0] - 2, N[l][1] - 2, N[l][2] - 2);
   }
-  if (h->lv[0].g.len >= (i64)1 << 31)
-    return fail(h, MG_ERR_ARG, "grid too large: padded arrays must stay below 2^31 elements");
   const Geom& gc = h->lv[L - 1].g;
   h->nc = (int)gc.npts();
-  if (h->nc > MG_MAX_COARSE) return fail(h, MG_ERR_ARG, "coarsest level exceeds MG_MAX_COARSE unknowns");
-  // telescoping: first level whose unknowns fit the bottom kernel
-  h->lb = L - 1;
-  while (h->lb > 0 && h->lv[h->lb - 1].g.npts() <= (i64)p.telescope_max_n && L - (h->lb - 1) <= BOT_MAX) --h->lb;
   // In float64 the bottom kernel's passes are bound by the float64 pipe of
   // its SM: a finest bottom level of more than one point per thread spreads
   // over a cluster of up to 8 blocks (8 SMs).  The float32 passes are bound
@@ -1197,8 +1379,14 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
 
 void release(mg_handle* h) {
   if (!h) return;
+  if (h->sub) {  // a slab sub-hierarchy owns only its buffers
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+    return;
+  }
   if (h->vexec) cudaGraphExecDestroy(h->vexec);
   if (h->s) cudaStreamSynchronize(h->s);
+  for (mg_handle* c : h->slab) release(c);
   for (void* p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (auto& pr : h->gap_ev)
@@ -1213,11 +1401,12 @@ void release(mg_handle* h) {
   delete h;
 }
 
-// Runs the V-cycle (and, in mixed precision, the casts around it); through a
-// CUDA graph captured on first use when the handle enables graphs.
 // kernel classes launched inside the V-cycle (and its graph)
 constexpr int VCYCLE_CLASSES = (1 << MG_K_CHEB_ZERO) | (1 << MG_K_CHEB_STEP) | (1 << MG_K_RESID) |
                                (1 << MG_K_RESTRICT) | (1 << MG_K_PROLONG) | (1 << MG_K_BOTTOM) | (1 << MG_K_DOT);
+
+// Runs the V-cycle (and, in mixed precision, the casts around it); through a
+// CUDA graph captured on first use when the handle enables graphs.
 
 template <class I, class TV> mg_status run_precondition(mg_handle* h, TV** z) {
   if (!h->prm.use_graph || (h->timing && (h->t_cls_mask & VCYCLE_CLASSES))) {  // timed launches run eagerly
@@ -1380,6 +1569,377 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
   h->st.rel_resid = bb > 0 ? std::sqrt(rr / bb) : 0.0;
   h->st.true_rel_resid = bb > 0 ? std::sqrt(h->hsc->true_rr / bb) : 0.0;
   h->st.solve_s = secs(t0);
+  h->st.kernel_launches = h->launches - launches0;
+  if (st) *st = h->st;
+  return result;
+}
+
+// ---- z-slab decomposition ----------------------------------------------------
+// The levels above the agglomeration level are split into z-slabs
+// (plan_slabs).  Each slab is a sub-hierarchy with the layout of a level of
+// its own (Geom with its plane count) whose two pad planes hold the
+// neighbouring slabs' boundary planes instead of zeros wherever a neighbour
+// exists: the halo that a rank of a distributed run receives into a local
+// buffer.  The kernels are those of the single-domain solve, unchanged; what
+// the decomposition adds is
+//   - the halo exchange of a pass's operand before every stencil or transfer
+//     pass (the operand's boundary planes copied into the neighbours' pad
+//     planes);
+//   - every reduction finished in two steps: each slab's block sums, then the
+//     slabs' sums added in slab order (the all-reduce);
+//   - the agglomeration: the agglomeration level's right-hand side gathered
+//     from the slabs into the root hierarchy (the handle's own), the root's
+//     V-cycle from there down (its bottom kernel), and the correction
+//     scattered back with one halo plane on each side.
+// All slabs live on the handle's device and stream: a single-GPU execution of
+// the decomposed algorithm, in which each copy stands for a peer copy or a
+// send/receive between ranks.  Setup builds the global hierarchy and copies
+// each slab's planes of the level operators (with their halo planes) out of
+// it.  A slab records the launches of one V-cycle and of one CG iteration
+// once; the solve replays every recorded pass on all slabs in turn.
+
+// Copies the planes of a slab out of a global level array: local planes
+// -1 .. nz_local (the halo planes included) from global planes z0-1 .. z1,
+// together with the pad slots just outside them that a 27-point stencil reads.
+mg_status copy_slab_planes(mg_handle* h, void* dst, const Geom& gl, const void* src, const Geom& gg, int z0, size_t es) {
+  const i64 lo_l = gl.Px - 1, lo_g = (i64)z0 * gg.sz + gg.Px - 1, n = gl.len - lo_l;
+  CK(cudaMemcpyAsync((char*)dst + lo_l * es, (const char*)src + lo_g * es, (size_t)n * es, cudaMemcpyDeviceToDevice,
+                     h->s));
+  return MG_OK;
+}
+
+mg_status build_slabs(mg_handle* h) {
+  const mg_params& p = h->prm;
+  const int S = p.slabs;
+  int la = 0;
+  {
+    const std::string e = plan_slabs(h->lv[0].N[0], h->lv[0].N[1], h->lv[0].N[2], p, &h->slab_z0, &la);
+    if (!e.empty()) return fail(h, MG_ERR_ARG, e);
+  }
+  h->nslab = S;
+  h->la = la;
+  AL(h->slots, double, 2 * (i64)S);
+  const size_t vb = vbytes(h), cb = cbytes(h);
+  const bool mixed = p.precision != MG_FP64;
+  for (int s = 0; s < S; ++s) {
+    mg_handle* c = new (std::nothrow) mg_handle();
+    if (!c) return fail(h, MG_ERR_ALLOC, "host allocation failed");
+    h->slab.push_back(c);
+    c->sub = true;
+    c->prm = p;
+    c->s = h->s;
+    c->us = h->us;
+    c->nsm = h->nsm;
+    c->dsc = h->dsc;
+    c->hsc = h->hsc;
+    c->dflag = h->dflag;
+    c->L = la + 1;
+    c->lb = la;
+    c->zvec = h->zvec;
+    c->lin_grid = h->lin_grid;
+    for (int l = 0; l <= la; ++l) {
+      const LevelBuf& G = h->lv[l];
+      LevelBuf& Lv = c->lv[l];
+      const int z0 = h->slab_z0[(size_t)l * (S + 1) + s], z1 = h->slab_z0[(size_t)l * (S + 1) + s + 1];
+      for (int a = 0; a < 3; ++a) {
+        Lv.N[a] = G.N[a];
+        Lv.ih2[a] = G.ih2[a];
+      }
+      Lv.N[2] = z1 - z0 + 2;
+      Lv.g = make_geom(G.g.nx, G.g.ny, z1 - z0);
+      Lv.beta = G.beta;
+      Lv.alpha = G.alpha;
+      Lv.g27 = G.g27;
+      const i64 n = Lv.g.len;
+      void* q;
+      mg_handle* hh = h;
+      auto slab_copy = [&](void** dst, const void* src, size_t es, int count) -> mg_status {
+        if (!src) return MG_OK;
+        void* d = nullptr;
+        mg_status st = alloc<char>(hh, (char**)&d, n * (i64)es * count);
+        if (st != MG_OK) return st;
+        for (int o = 0; o < count; ++o) {
+          st = copy_slab_planes(hh, (char*)d + (size_t)o * n * es, Lv.g, (const char*)src + (size_t)o * G.g.len * es,
+                                G.g, z0, es);
+          if (st != MG_OK) return st;
+        }
+        *dst = d;
+        return MG_OK;
+      };
+      mg_status st = MG_OK;
+      if (l < la) {  // the operators of the slab's levels
+        if (G.g27) {
+          if ((st = slab_copy(&Lv.w, G.w, cb, 13)) != MG_OK) return st;
+          if ((st = slab_copy(&Lv.dg, G.dg, vb, 1)) != MG_OK) return st;
+        } else {
+          if ((st = slab_copy(&Lv.kx, G.kx, cb, 1)) != MG_OK) return st;
+          if ((st = slab_copy(&Lv.ky, G.ky, cb, 1)) != MG_OK) return st;
+          if ((st = slab_copy(&Lv.kz, G.kz, cb, 1)) != MG_OK) return st;
+          if (l == 0 && mixed) {
+            void* t = nullptr;
+            if ((st = slab_copy(&t, G.kx64, 8, 1)) != MG_OK) return st;
+            Lv.kx64 = (double*)t;
+            if ((st = slab_copy(&t, G.ky64, 8, 1)) != MG_OK) return st;
+            Lv.ky64 = (double*)t;
+            if ((st = slab_copy(&t, G.kz64, 8, 1)) != MG_OK) return st;
+            Lv.kz64 = (double*)t;
+          } else if (!mixed) {
+            Lv.kx64 = (double*)Lv.kx;
+            Lv.ky64 = (double*)Lv.ky;
+            Lv.kz64 = (double*)Lv.kz;
+          }
+        }
+        if ((st = slab_copy(&Lv.dinv, G.dinv, vb, 1)) != MG_OK) return st;
+      }
+      for (void** v : {&Lv.x[0], &Lv.x[1], &Lv.d, &Lv.r}) {
+        st = alloc<char>(c, (char**)&q, n * (i64)vb);
+        if (st != MG_OK) return fail(h, st, c->err);
+        *v = q;
+      }
+      if (l > 0 || mixed) {
+        st = alloc<char>(c, (char**)&q, n * (i64)vb);
+        if (st != MG_OK) return fail(h, st, c->err);
+        Lv.b = q;
+      }
+    }
+    // the slab's float64 CG vectors and finest diagonal
+    const Geom& g0 = c->lv[0].g;
+    for (double** v : {&c->cb, &c->cx, &c->cr, &c->cq, &c->cp, &c->cw}) {
+      mg_status st = alloc<double>(c, v, g0.len);
+      if (st != MG_OK) return fail(h, st, c->err);
+    }
+    {
+      void* t = nullptr;
+      mg_handle* hh = h;
+      mg_status st = alloc<char>(hh, (char**)&t, g0.len * 8);
+      if (st != MG_OK) return st;
+      if ((st = copy_slab_planes(hh, t, g0, h->dg64, h->lv[0].g, h->slab_z0[s], 8)) != MG_OK) return st;
+      c->dg64 = (double*)t;
+    }
+    if (!mixed) c->lv[0].b = c->cr;
+    // reduction scratch of the slab's largest reducing launch
+    int kcz;
+    dim3 gz = zm_grid(c, g0, &kcz);
+    dim3 gv = zv_grid(c, g0, &kcz);
+    c->pstride = std::max((int)(gz.x * gz.y * gz.z), std::max((int)(gv.x * gv.y * gv.z), c->lin_grid));
+    {
+      mg_status st = alloc<double>(c, &c->partials, 2 * (i64)c->pstride);
+      if (st != MG_OK) return fail(h, st, c->err);
+    }
+    c->lin_lo = g0.off;
+    c->lin_hi = g0.off + (i64)g0.nz * g0.sz;
+  }
+  CKL();
+  return MG_OK;
+}
+
+// Before a pass: each pair of neighbouring slabs swaps the operand's boundary
+// planes into each other's pad planes (a slab's last plane to the next slab's
+// lower pad plane, the next slab's first plane to its upper pad plane).
+mg_status slab_exchange(mg_handle* h, const std::vector<std::vector<Pass>>& R, size_t i) {
+  for (int s = 0; s + 1 < h->nslab; ++s) {
+    const Pass& a = R[s][i];
+    const Pass& b = R[s + 1][i];
+    const size_t es = (size_t)a.halo_bytes, pb = (size_t)a.halo_g.sz * es;
+    char* A = (char*)a.halo;
+    char* B = (char*)b.halo;
+    const Geom &ga = a.halo_g, &gb = b.halo_g;
+    CK(cudaMemcpyAsync(B + (size_t)(gb.off - gb.sz) * es, A + (size_t)(ga.off + (i64)(ga.nz - 1) * ga.sz) * es, pb,
+                       cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(A + (size_t)(ga.off + (i64)ga.nz * ga.sz) * es, B + (size_t)gb.off * es, pb,
+                       cudaMemcpyDeviceToDevice, h->s));
+  }
+  return MG_OK;
+}
+
+// A reduction finished across the slabs: each slab's block sums into its
+// slot, then the slots added in slab order and the CG scalars updated.
+void slab_finish(mg_handle* h, const int* nbs, int mode) {
+  const int S = h->nslab;
+  for (int s = 0; s < S; ++s)
+    launch(h, k_finish_partial, dim3(1), dim3(256), 0, (const double*)h->slab[s]->partials, nbs[s],
+           h->slab[s]->pstride, h->slots + s, S);
+  launch(h, k_combine, dim3(1), dim3(32), 0, (const double*)h->slots, S, mode, h->dsc, h->prm.flexible);
+  h->launches += S + 1;
+}
+
+// The agglomeration level: gather the slabs' right-hand sides into the root
+// level, run the root's V-cycle from it, scatter its correction (with one halo
+// plane on each side) back to the slabs.
+template <class I> mg_status slab_agglomerate(mg_handle* h, int la) {
+  using TV = typename I::TVt;
+  const int S = h->nslab;
+  LevelBuf& R = h->lv[la];
+  const i64 sz = R.g.sz;
+  for (int s = 0; s < S; ++s) {
+    const LevelBuf& C = h->slab[s]->lv[la];
+    const int z0 = h->slab_z0[(size_t)la * (S + 1) + s];
+    CK(cudaMemcpyAsync((TV*)R.b + R.g.off + (i64)z0 * sz, (const TV*)C.b + C.g.off, (size_t)C.g.nz * sz * sizeof(TV),
+                       cudaMemcpyDeviceToDevice, h->s));
+  }
+  const int cur = I::vcycle(h, la);
+  for (int s = 0; s < S; ++s) {
+    LevelBuf& C = h->slab[s]->lv[la];
+    const int z0 = h->slab_z0[(size_t)la * (S + 1) + s];
+    CK(cudaMemcpyAsync((TV*)C.x[0] + C.g.off - sz, (const TV*)R.x[cur] + R.g.off + (i64)(z0 - 1) * sz,
+                       (size_t)(C.g.nz + 2) * sz * sizeof(TV), cudaMemcpyDeviceToDevice, h->s));
+  }
+  return MG_OK;
+}
+
+// Replays a recorded phase on all slabs, pass by pass.
+template <class I> mg_status slab_replay(mg_handle* h, const std::vector<std::vector<Pass>>& R) {
+  const int S = h->nslab;
+  std::vector<int> nbs(S);
+  mg_status st;
+  for (size_t i = 0; i < R[0].size(); ++i) {
+    const Pass& p0 = R[0][i];
+    switch (p0.kind) {
+      case Pass::LAUNCH:
+        if (p0.halo && (st = slab_exchange(h, R, i)) != MG_OK) return st;
+        for (int s = 0; s < S; ++s) R[s][i].fn();
+        h->launches += S;
+        break;
+      case Pass::MEMSET:
+        for (int s = 0; s < S; ++s) R[s][i].fn();
+        break;
+      case Pass::FINISH:
+        for (int s = 0; s < S; ++s) nbs[s] = R[s][i].nb;
+        slab_finish(h, nbs.data(), p0.mode);
+        break;
+      case Pass::AGGLOM:
+        if ((st = slab_agglomerate<I>(h, p0.level)) != MG_OK) return st;
+        break;
+    }
+  }
+  CKL();
+  return MG_OK;
+}
+
+// Records one V-cycle and one CG iteration of every slab (once per handle).
+template <class I, bool FLEX> mg_status slab_record(mg_handle* h) {
+  using TV = typename I::TVt;
+  if (!h->vrec.empty()) return MG_OK;
+  const int S = h->nslab;
+  h->vrec.assign(S, {});
+  h->crec.assign(S, {});
+  h->vz.assign(S, nullptr);
+  for (int s = 0; s < S; ++s) {
+    mg_handle* c = h->slab[s];
+    c->rec = &h->vrec[s];
+    TV* z = I::precondition(c);
+    c->rec = &h->crec[s];
+    cg_iteration<I, FLEX>(c, z, c->lv[0].g, c->lv[0]);
+    c->rec = nullptr;
+    h->vz[s] = z;
+  }
+  for (int s = 1; s < S; ++s) {  // every slab runs the same passes
+    if (h->vrec[s].size() != h->vrec[0].size() || h->crec[s].size() != h->crec[0].size())
+      return fail(h, MG_ERR_ARG, "slab sub-hierarchies recorded different pass sequences");
+    for (size_t i = 0; i < h->vrec[0].size(); ++i)
+      if (h->vrec[s][i].kind != h->vrec[0][i].kind) return fail(h, MG_ERR_ARG, "slab pass sequences differ");
+  }
+  return MG_OK;
+}
+
+// The decomposed CG solve: the steps of solve_impl with every vector split
+// over the slabs.
+template <class I> mg_status slab_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  auto t0 = clk::now();
+  const mg_params& p = h->prm;
+  const int S = h->nslab;
+  const Geom& gG = h->lv[0].g;
+  const i64 plane = (i64)(gG.nx + 2) * (gG.ny + 2);  // elements per dense full-grid plane
+  h->hist.clear();
+  const long long launches0 = h->launches;
+  mg_status s;
+  if ((s = p.flexible ? slab_record<I, true>(h) : slab_record<I, false>(h)) != MG_OK) return s;
+  std::vector<int> nbs(S);
+  CK(cudaMemsetAsync(h->dsc, 0, sizeof(Scal), h->s));
+  for (int q = 0; q < S; ++q) {
+    mg_handle* c = h->slab[q];
+    const Geom& g = c->lv[0].g;
+    k_pack<double><<<lin_blocks(h, g.npts()), 256, 0, h->s>>>(f + (i64)h->slab_z0[q] * plane, c->cb, g);
+    CK(cudaMemsetAsync(c->cx, 0, (size_t)g.len * 8, h->s));
+    CK(cudaMemsetAsync(c->cp, 0, (size_t)g.len * 8, h->s));
+    CK(cudaMemcpyAsync(c->cr, c->cb, (size_t)g.len * 8, cudaMemcpyDeviceToDevice, h->s));
+    nbs[q] = linear<true>(c, g.len, LinDot<double>{c->cb, c->cb});
+  }
+  slab_finish(h, nbs.data(), FIN_BB);
+  if ((s = read_scal(h)) != MG_OK) return s;
+  Scal sc = *h->hsc;
+  mg_status result = MG_OK;
+  int it = 0;
+  const double bb = sc.bb;
+  if (sc.status & 1) return fail(h, MG_ERR_NONFINITE, "non-finite value in f");
+  const double tol2 = rtol * rtol * bb;
+  double rr = sc.rr;
+  if (bb > 0) h->hist.push_back(std::sqrt(rr / bb));
+  if (bb > 0 && rr > tol2) {
+    for (int q = 0; q < S; ++q) I::cast_rhs(h->slab[q]);
+    if ((s = slab_replay<I>(h, h->vrec)) != MG_OK) return s;
+    for (it = 1; it <= p.maxit; ++it) {
+      if ((s = slab_replay<I>(h, h->crec)) != MG_OK) return s;
+      if ((s = read_scal(h)) != MG_OK) return s;
+      sc = *h->hsc;
+      if (sc.status & 1) {
+        result = fail(h, MG_ERR_NONFINITE, "non-finite value during the iteration");
+        break;
+      }
+      if (sc.status & 2) {
+        result = fail(h, MG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0");
+        break;
+      }
+      rr = sc.rr;
+      h->hist.push_back(std::sqrt(rr / bb));
+      if (rr <= tol2) break;
+      if (it == p.maxit) {
+        result = fail(h, MG_ERR_NOT_CONVERGED, "maximum number of iterations reached");
+        break;
+      }
+      if ((s = slab_replay<I>(h, h->vrec)) != MG_OK) return s;
+    }
+    if (it > p.maxit) it = p.maxit;
+    for (int q = 0; q < S; ++q) {
+      mg_handle* c = h->slab[q];
+      linear<false>(c, c->lv[0].g.len, LinXUpd{c->cx, c->cp, h->dsc, 0.0});
+    }
+  }
+  // x: each slab writes its own planes (the first and last slab also the boundary planes)
+  for (int q = 0; q < S; ++q) {
+    mg_handle* c = h->slab[q];
+    const Geom& g = c->lv[0].g;
+    const int kf = q == 0 ? 0 : 1, kl = q == S - 1 ? g.nz + 1 : g.nz;
+    k_unpack<double><<<lin_blocks(h, (i64)(g.nx + 2) * (g.ny + 2) * (kl - kf + 1)), 256, 0, h->s>>>(
+        c->cx, x + (i64)h->slab_z0[q] * plane, g, kf, kl);
+  }
+  // true residual in float64: halo exchange of x, residual and its norm per slab
+  {
+    std::vector<std::vector<Pass>> R(S, std::vector<Pass>(1));
+    for (int q = 0; q < S; ++q) {
+      R[q][0].halo = h->slab[q]->cx;
+      R[q][0].halo_bytes = 8;
+      R[q][0].halo_g = h->slab[q]->lv[0].g;
+    }
+    if ((s = slab_exchange(h, R, 0)) != MG_OK) return s;
+    for (int q = 0; q < S; ++q) {
+      mg_handle* c = h->slab[q];
+      const LevelBuf& C0 = c->lv[0];
+      OpResidual<double, double, double, double> res{c->cx, c->cb, c->cq, C0.kx64, C0.ky64, C0.kz64};
+      nbs[q] = zmarch<true>(c, C0.g, res);
+    }
+    slab_finish(h, nbs.data(), FIN_TRUE);
+  }
+  if ((s = read_scal(h)) != MG_OK) return s;
+  h->st.iters = it;
+  h->st.bnorm = std::sqrt(bb);
+  h->st.rel_resid = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  h->st.true_rel_resid = bb > 0 ? std::sqrt(h->hsc->true_rr / bb) : 0.0;
+  h->st.solve_s = secs(t0);
+  for (mg_handle* c : h->slab) {
+    h->launches += c->launches;
+    c->launches = 0;
+  }
   h->st.kernel_launches = h->launches - launches0;
   if (st) *st = h->st;
   return result;
@@ -1613,6 +2173,8 @@ mg_status mg_params_default(mg_params* p) {
   p->coarse_maxit = 30;
   p->bottom_blocks = 0;
   p->test_inject = 0;
+  p->slabs = 1;
+  p->slab_level = 0;
   return MG_OK;
 }
 
@@ -1634,7 +2196,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256 || p.eig_mode < 0 ||
       p.eig_mode > 1 || !(p.eig_safety > 0.0) || p.coarse_solve < 0 || p.coarse_solve > 1 ||
       !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32 || (p.bottom_blocks != 0 && p.bottom_blocks != 1 && p.bottom_blocks != 2 && p.bottom_blocks != 4 && p.bottom_blocks != 8) ||
-      p.test_inject < 0 || p.test_inject > 3)
+      p.test_inject < 0 || p.test_inject > 3 || p.slabs < 1 || p.slabs > MG_MAX_SLABS || p.slab_level < 0 ||
+      (p.slabs > 1 && (p.krylov != MG_KRYLOV_CG || p.stencil_kernel == 1 || p.nonzero_guess)))
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
   // V-cycles need the same iteration counts with it as with the flexible
@@ -1665,6 +2228,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   }
   Guard guard(s == MG_OK ? h : nullptr);
   if (s == MG_OK) s = build_hierarchy(h, Nx, Ny, Nz, k_cells, k_on_device);
+  if (s == MG_OK && p.slabs > 1) s = build_slabs(h);
+  if (s == MG_OK) s = sync_check(h);
   if (s != MG_OK) {
     g_setup_error = h->err;
     guard.h = nullptr;
@@ -1685,9 +2250,25 @@ mg_status mg_set_stream(mg_handle* h, void* stream) {
 mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
   if (!h || !f || !x || !(rtol >= 0)) return h ? fail(h, MG_ERR_ARG, "null pointer or negative rtol") : MG_ERR_ARG;
   Guard guard(h);
+  if (h->nslab > 1) return dispatch(h, [&](auto impl) { return slab_solve<decltype(impl)>(h, f, x, rtol, st); });
   if (h->prm.krylov == MG_KRYLOV_FGMRES)
     return dispatch(h, [&](auto impl) { return fgmres_impl<decltype(impl)>(h, f, x, rtol, st); });
   return dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, f, x, rtol, st); });
+}
+
+mg_status mg_slab_plan(int Nx, int Ny, int Nz, const mg_params* p, int* bounds, int cap, int* agglomerate_level) {
+  if (!p || !bounds || !agglomerate_level || p->slabs < 1 || p->slabs > MG_MAX_SLABS || p->slab_level < 0 ||
+      p->telescope_max_n < 0)
+    return fail(nullptr, MG_ERR_ARG, "invalid mg_slab_plan arguments");
+  if (Nx < 3 || Ny < 3 || Nz < 3) return fail(nullptr, MG_ERR_ARG, "grid needs at least 3 vertices per axis");
+  std::vector<int> b;
+  int la = 0;
+  const std::string e = plan_slabs(Nx, Ny, Nz, *p, &b, &la);
+  if (!e.empty()) return fail(nullptr, MG_ERR_ARG, e);
+  if ((int)b.size() > cap) return fail(nullptr, MG_ERR_ARG, "bounds array too small: (agglomeration level + 1) x (slabs + 1) entries");
+  std::copy(b.begin(), b.end(), bounds);
+  *agglomerate_level = la;
+  return MG_OK;
 }
 
 mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, double rtol, mg_stats* st) {
@@ -1703,7 +2284,9 @@ mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, doub
   CK(cudaMemcpyAsync(h->hstage[0], f_host, bytes, cudaMemcpyHostToDevice, h->s));
   if (h->prm.nonzero_guess) CK(cudaMemcpyAsync(h->hstage[1], x_host, bytes, cudaMemcpyHostToDevice, h->s));
   mg_status s;
-  if (h->prm.krylov == MG_KRYLOV_FGMRES)
+  if (h->nslab > 1)
+    s = dispatch(h, [&](auto impl) { return slab_solve<decltype(impl)>(h, h->hstage[0], h->hstage[1], rtol, st); });
+  else if (h->prm.krylov == MG_KRYLOV_FGMRES)
     s = dispatch(h, [&](auto impl) { return fgmres_impl<decltype(impl)>(h, h->hstage[0], h->hstage[1], rtol, st); });
   else
     s = dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, h->hstage[0], h->hstage[1], rtol, st); });

@@ -47,12 +47,12 @@ __global__ void __launch_bounds__(ZM_THREADS, ZmMinBlocks<Op>::value) k_zmarch(O
 // per step, fixed grid, deterministic per-block sums as in k_zmarch.
 constexpr int LIN_THREADS = 256;
 template <class Op, bool RED>
-__global__ void __launch_bounds__(LIN_THREADS) k_linear(Op op, i64 n, double* partials, int stride) {
+__global__ void __launch_bounds__(LIN_THREADS) k_linear(Op op, i64 lo, i64 n, double* partials, int stride) {
   pdl_wait();
   op.prepare();
   double a0 = 0.0, a1 = 0.0;
   const i64 step = (i64)gridDim.x * LIN_THREADS * 4;
-  for (i64 t = ((i64)blockIdx.x * LIN_THREADS + threadIdx.x) * 4; t < n; t += step) op.pt4(t, a0, a1);
+  for (i64 t = lo + ((i64)blockIdx.x * LIN_THREADS + threadIdx.x) * 4; t < n; t += step) op.pt4(t, a0, a1);
   pdl_trigger();
   if constexpr (RED) {
     block_sum2<LIN_THREADS>(a0, a1);
@@ -117,18 +117,20 @@ __global__ void k_pack(const double* __restrict__ src, T* __restrict__ dst, Geom
   }
 }
 
-// padded interior array of type T -> dense full-grid float64 with zero boundary
+// padded interior array of type T -> dense full-grid float64 with zero
+// boundary, full-grid planes K = kfirst .. klast (0 .. nz+1 for the whole
+// grid; a z-slab writes only the planes it owns)
 template <class T>
-__global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, Geom g) {
-  const int Nx = g.nx + 2, Ny = g.ny + 2, Nz = g.nz + 2;
-  const i64 n = (i64)Nx * Ny * Nz;
+__global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, Geom g, int kfirst, int klast) {
+  const int Nx = g.nx + 2, Ny = g.ny + 2;
+  const i64 n = (i64)Nx * Ny * (klast - kfirst + 1);
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
     const int I = (int)(t % Nx);
     const i64 r = t / Nx;
     const int J = (int)(r % Ny);
-    const int K = (int)(r / Ny);
+    const int K = kfirst + (int)(r / Ny);
     const bool in = I >= 1 && I <= g.nx && J >= 1 && J <= g.ny && K >= 1 && K <= g.nz;
-    dst[t] = in ? cvt<double>(src[g.at(I - 1, J - 1, K - 1)]) : 0.0;
+    dst[((i64)K * Ny + J) * Nx + I] = in ? cvt<double>(src[g.at(I - 1, J - 1, K - 1)]) : 0.0;
   }
 }
 
@@ -357,18 +359,8 @@ template <class TV> __global__ void k_lz_xpay(TV* y, const TV* x, double b, i64 
 // ------------------------------------------------------------ scalars
 enum FinishMode { FIN_BB = 0, FIN_RR = 1, FIN_RZ0 = 2, FIN_PQ = 3, FIN_RZ = 4, FIN_TRUE = 5 };
 
-// Sums partials[0..n) (and partials[stride..stride+n)) in a fixed order and
-// updates the CG scalars.  One block of 256 threads.
-__global__ void __launch_bounds__(256) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
-                                                int flexible) {
-  pdl_wait();
-  double a0 = 0.0, a1 = 0.0;
-  for (int t = threadIdx.x; t < n; t += 256) {
-    a0 += partials[t];
-    a1 += partials[stride + t];
-  }
-  block_sum2<256>(a0, a1);
-  if (threadIdx.x != 0) return;
+// The CG scalar update of a finished reduction (a0, a1) in the given mode.
+__device__ __forceinline__ void finish_apply(double a0, double a1, int mode, Scal* s, int flexible) {
   switch (mode) {
     case FIN_BB:
       s->bb = a0;
@@ -405,6 +397,50 @@ __global__ void __launch_bounds__(256) k_finish(const double* partials, int n, i
       break;
     }
   }
+}
+
+// Sums partials[0..n) (and partials[stride..stride+n)) in a fixed order and
+// updates the CG scalars.  One block of 256 threads.
+__global__ void __launch_bounds__(256) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
+                                                int flexible) {
+  pdl_wait();
+  double a0 = 0.0, a1 = 0.0;
+  for (int t = threadIdx.x; t < n; t += 256) {
+    a0 += partials[t];
+    a1 += partials[stride + t];
+  }
+  block_sum2<256>(a0, a1);
+  if (threadIdx.x == 0) finish_apply(a0, a1, mode, s, flexible);
+}
+
+// z-slab decomposition: one slab's reduction summed as k_finish sums it, into
+// slot[0] and slot[nslab] instead of the scalars ...
+__global__ void __launch_bounds__(256) k_finish_partial(const double* partials, int n, int stride, double* slot,
+                                                        int nslab) {
+  pdl_wait();
+  double a0 = 0.0, a1 = 0.0;
+  for (int t = threadIdx.x; t < n; t += 256) {
+    a0 += partials[t];
+    a1 += partials[stride + t];
+  }
+  block_sum2<256>(a0, a1);
+  if (threadIdx.x == 0) {
+    slot[0] = a0;
+    slot[nslab] = a1;
+  }
+}
+
+// ... and the slabs' sums added in slab order (the all-reduce of a
+// decomposed dot product), then the scalar update.
+__global__ void k_combine(const double* slots, int nslab, int mode, Scal* s, int flexible) {
+  pdl_wait();
+  if (threadIdx.x != 0) return;
+  double a0 = 0.0, a1 = 0.0;
+  for (int q = 0; q < nslab; ++q) {
+    a0 += slots[q];
+    a1 += slots[nslab + q];
+  }
+  finish_apply(a0, a1, mode, s, flexible);
 }
 
 // ------------------------------------------------------------ gradient

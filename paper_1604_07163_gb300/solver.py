@@ -45,6 +45,8 @@ class Params:
     coarse_maxit: int = 30
     bottom_blocks: int = 0  # 0 automatic; 1 one block; 2, 4, 8 a thread-block cluster
     test_inject: int = 0  # test only: 1 negated outer diagonal (breakdown), 2 negated coarsest diagonal (not SPD)
+    slabs: int = 1  # z-slab decomposition of the solve (1: none)
+    slab_level: int = 0  # agglomeration level of the slabs (0: the bottom kernel's first level)
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -64,6 +66,8 @@ class Params:
         p.coarse_maxit = self.coarse_maxit
         p.bottom_blocks = self.bottom_blocks
         p.test_inject = self.test_inject
+        p.slabs = self.slabs
+        p.slab_level = self.slab_level
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p

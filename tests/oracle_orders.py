@@ -19,10 +19,12 @@ def check_fp64_solve_against_both_oracle_orders(xg, itg, hist, f, k, rtol, oracl
       oracle is run for exactly itg iterations when its own count differs):
       two runs that stop one iteration apart differ by that iteration's
       update whatever their rounding, which is not a parity defect.  The GPU
-      must then be within relative 1e-10 in the 2-norm of one order, or no
-      farther from either order than the two orders are from each other
-      (plus 1e-10): rounding order alone moves a high-contrast solve by more
-      than 1e-10, and the oracle's own spread measures by how much.
+      must then be within relative 1e-10 in the 2-norm of one order.  Where
+      rounding order alone moves a high-contrast solve by more than that, the
+      oracle's two orders measure by how much (their distance d): the GPU's
+      sums are a third fixed order, so it must be no farther than d from the
+      nearer oracle order and, by the triangle inequality, no farther than
+      2 d from the other (each plus 1e-10).
     - The residual history follows the nearest order's over hist_its
       iterations (all when None).
     Returns (errors at equal iterations, oracle spread at equal iterations)."""
@@ -38,7 +40,8 @@ def check_fp64_solve_against_both_oracle_orders(xg, itg, hist, f, k, rtol, oracl
     assert min(abs(itg - i) for i in its) <= 1, (itg, its)
     spread = rel2(at_itg[1], at_itg[0])
     errs = [rel2(xg, x) for x in at_itg]
-    assert min(errs) <= 1e-10 or max(errs) <= spread + 1e-10, (itg, its, errs, spread)
+    assert min(errs) <= 1e-10 or (min(errs) <= spread + 1e-10 and max(errs) <= 2 * spread + 1e-10), (
+        itg, its, errs, spread)
     ho = hists[0] if abs(itg - its[0]) <= abs(itg - its[1]) else hists[1]
     h = np.asarray(hist)
     m = min(len(h), len(ho), hist_its or len(h))

@@ -152,3 +152,17 @@ def test_513_galerkin_target_solve(gpu_lib):
     # equal final accuracy: the two forms agree to what the tolerance implies
     assert rel2(sols["mixed_fp32"][0], sols["fp64"][0]) < 1e-6
     assert sols["mixed_fp32"][1] <= 1.1 * sols["fp64"][1]
+
+
+def test_257_slab_decomposition_solve(gpu_lib, w257):
+    """The benchmark workload decomposed into 4 z-slabs (agglomerated at the
+    15^3 bottom level): float64 parity against the oracle's solves and the
+    float32-V-cycle form's true residual by the oracle's operator."""
+    mg = gpu_lib
+    dims, k, f, spec, O = w257
+    x, st = mg.MGSolver(T(k), mg.Params(maxit=3000, slabs=4)).solve(T(f), spec["rtol"])
+    check_fp64_solve_against_both_oracle_orders(x.cpu().numpy(), st.iters, st.history, f, k, spec["rtol"],
+                                                hist_its=10)
+    x32, st32 = mg.MGSolver(T(k), mg.Params(maxit=3000, slabs=4, precision="mixed_fp32")).solve(T(f), spec["rtol"])
+    true = np.linalg.norm((f - O.apply(x32.cpu().numpy()))[1:-1, 1:-1, 1:-1]) / np.linalg.norm(f)
+    assert true <= spec["rtol"] * 1.01
