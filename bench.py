@@ -151,7 +151,7 @@ def whole_job_dofs_per_s(unknowns_per_rank: int, world: int, ms_per_step: float)
     return world * unknowns_per_rank / (ms_per_step * 1e-3)
 
 
-def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised"):
+def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised", slabs=1):
     N = spec["N"]
     levels = 1
     M = N
@@ -165,7 +165,8 @@ def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op=
                     f"operators), V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual "
                     f"{spec['rtol']:g}" + ("; step = forward + adjoint solve with the cell gradient" if adjoint else ""),
         "l2": "no flush: inputs larger than L2 (each float64 vector 134 MB; working set > 2 GB)",
-        "parallelism": "replicas" if n_ranks > 1 else "single GPU",
+        "parallelism": ("replicas" if n_ranks > 1 else "single GPU")
+                       + (f", solve decomposed into {slabs} z-slabs" if slabs > 1 else ""),
     }
     return d
 
@@ -302,7 +303,7 @@ def run_ours(args):
 
     for form in (run_forms if not args.only_paper_configs else []):
         S = mg.MGSolver(k, mg.Params(precision=form, maxit=args.maxit, face_rule=args.face_rule,
-                                     coarse_op=args.coarse_op))
+                                     coarse_op=args.coarse_op, slabs=args.slabs))
         headline = form == HEADLINE
         profile_all = None
         for w in range(args.warmup):
@@ -377,14 +378,26 @@ def run_ours(args):
         for _ in range(args.warmup):
             S.solve(f, rtol, raise_on_error=False)
         msg, outs = timed(lambda: S.solve(f, rtol, raise_on_error=False), args.steps)
-        stg = outs[-1][1]
+        xg, stg = outs[-1]
         out = {"value": whole_job_dofs_per_s(n, world, msg), "unit": "DOF/s", "ms_per_step": msg,
                "iters": stg.iters, "true_rel_resid": stg.true_rel_resid, "status": stg.status,
                "precision": HEADLINE, **{k_: v_ for k_, v_ in extra.items() if k_ != "maxit"}}
+        ref = solutions.get(HEADLINE)
+        if ref is not None:
+            out["rel_err_vs_headline_solution"] = float((xg - ref).norm() / ref.norm())
         S.close()
         del S
         return out
 
+    slabs = None
+    if world == 1 and not args.adjoint and not args.no_slabs and args.slabs == 1:
+        # the z-slab decomposition of the headline solve on this one GPU (slabs
+        # run one after another, each halo exchange a device copy): its cost
+        # over the single-domain solve and its distance from that solution
+        slabs = {}
+        for nsl in (2, 4):
+            out_s = timed_variant(slabs=nsl, coarse_op=args.coarse_op)
+            slabs[f"slabs{nsl}"] = out_s
     galerkin = paper = None
     if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_galerkin:
         galerkin = timed_variant(coarse_op="galerkin")
@@ -439,9 +452,9 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms[HEADLINE]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic", "precision": HEADLINE, "iterations": forms[HEADLINE]["iters"],
-        "config": config_dict(spec, world, args.workload, args.face_rule, args.adjoint, args.coarse_op),
+        "config": config_dict(spec, world, args.workload, args.face_rule, args.adjoint, args.coarse_op, args.slabs),
         "forms": forms, "speedup_mixed_vs_fp64": speedup, "target_513_c1e6": target,
-        "galerkin_coarse_operators": galerkin, "paper_configurations": paper,
+        "galerkin_coarse_operators": galerkin, "paper_configurations": paper, "slab_decomposition": slabs,
         "roofline": roofline, "smoother_roofline": smoother, "host_gap": host_gap, "cpu_baseline": cpu,
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
@@ -612,6 +625,10 @@ def main():
                     help="skip the 513^3 contrast-10^6 Galerkin target solve")
     ap.add_argument("--only-paper-configs", action="store_true",
                     help="time only the Galerkin variant and the paper's solver configurations (for profiling)")
+    ap.add_argument("--slabs", type=int, default=1,
+                    help="solve every form with the z-slab decomposition into this many slabs (1: none)")
+    ap.add_argument("--no-slabs", action="store_true",
+                    help="skip timing the headline form decomposed into 2 and 4 z-slabs")
     ap.add_argument("--maxit", type=int, default=3000)
     ap.add_argument("--adjoint", action="store_true", help="each step is a forward + adjoint solve with gradient")
     args = ap.parse_args()
