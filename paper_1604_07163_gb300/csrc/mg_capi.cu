@@ -75,6 +75,7 @@ struct mg_handle {
   cudaStream_t s = nullptr;   // internal non-blocking stream (graph capture needs one)
   cudaStream_t us = nullptr;  // caller's stream; ordered against s with events
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_scal = nullptr;  // the copy of the CG scalars to the host has landed
   int nsm = 152;
   int L = 0, lb = 0;  // levels; first level of the bottom kernel
   int bot_cluster = 1;  // blocks of the bottom kernel (a cluster when > 1)
@@ -97,7 +98,8 @@ struct mg_handle {
   double* partials = nullptr;
   int pstride = 0;
   Scal* dsc = nullptr;
-  Scal* hsc = nullptr;  // pinned host mirror
+  Scal* hsc = nullptr;      // pinned host mirror (mapped)
+  Scal* hsc_dev = nullptr;  // its device address (k_finish writes the outer iteration's scalars there)
   int* dflag = nullptr;
   std::vector<double> hist;
   std::string err;
@@ -507,7 +509,7 @@ template <bool RED, class Op> int linear(mg_handle* h, i64 n, const Op& op, int 
   return nb;
 }
 
-void finish(mg_handle* h, int nblocks, int mode) {
+void finish(mg_handle* h, int nblocks, int mode, Scal* mirror = nullptr) {
   if (h->rec) {  // a slab: the reduction is finished across the slabs at replay
     Pass ps;
     ps.kind = Pass::FINISH;
@@ -517,7 +519,8 @@ void finish(mg_handle* h, int nblocks, int mode) {
     return;
   }
   int flex = h->prm.flexible;
-  launch(h, k_finish, dim3(1), dim3(256), 0, (const double*)h->partials, nblocks, h->pstride, mode, h->dsc, flex);
+  launch(h, k_finish, dim3(1), dim3(256), 0, (const double*)h->partials, nblocks, h->pstride, mode, h->dsc, flex,
+         mirror);
   ++h->launches;
 }
 
@@ -1007,6 +1010,22 @@ mg_status read_scal(mg_handle* h) {
   return MG_OK;
 }
 
+// The same read in two halves, so that more work can be queued behind it
+// before the host waits.  The outer iteration's last reduction has already
+// written the scalars to the host (k_finish's mirror), so only an event is
+// queued; otherwise a copy.
+mg_status read_scal_issue(mg_handle* h, bool mirrored) {
+  CKL();
+  if (!mirrored) CK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(Scal), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaEventRecord(h->ev_scal, h->s));
+  return MG_OK;
+}
+mg_status read_scal_wait(mg_handle* h) {
+  CK(cudaEventSynchronize(h->ev_scal));
+  tm_collect(h);
+  return MG_OK;
+}
+
 // pack a dense float64 nodal array into a padded buffer of the level's vector type
 mg_status pack_level(mg_handle* h, int l, const double* src, void* dst, bool f64) {
   const Geom& g = h->lv[l].g;
@@ -1394,6 +1413,7 @@ void release(mg_handle* h) {
       if (e) cudaEventDestroy(e);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_scal) cudaEventDestroy(h->ev_scal);
   if (h->s) cudaStreamDestroy(h->s);
   if (h->dflag) cudaFree(h->dflag);
   if (h->hsc) cudaFreeHost(h->hsc);
@@ -1472,7 +1492,7 @@ mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
     nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, false>{h->cr, h->cq, z, nullptr, h->dsc, 0.0}, MG_K_CG_UPD);
   else
     nb = linear<true>(h, g.len, LinCgUpd<TV, FLEX, true>{h->cr, h->cq, z, (float*)L0.b, h->dsc, 0.0}, MG_K_CG_UPD);
-  finish(h, nb, FIN_RR);
+  finish(h, nb, FIN_RR, h->sub ? nullptr : h->hsc_dev);  // the host reads the scalars after this one
   return MG_OK;
 }
 
@@ -1514,19 +1534,36 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
     if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
     const bool gap_on = h->timing && ((h->t_cls_mask >> MG_K_HOST_GAP) & 1) && h->gap_ev[0][0];
     int gap_prev = -1;  // event pair recorded in the previous iteration, read after the next host sync
+    // The next V-cycle needs only the residual this iteration writes, so it is
+    // queued behind the copy of the CG scalars before the host waits for
+    // them: the host's convergence test then overlaps the device's work.  It
+    // is skipped when the last residual reduction predicts convergence in this
+    // iteration (a V-cycle queued after the last iteration would be wasted).
+    double rr_prev = rr, ratio = 1.0;
+    bool queued = false;  // the next V-cycle is already queued
     for (it = 1; it <= p.maxit; ++it) {
       if (p.flexible) cg_iteration<I, true>(h, z, g, L0);
       else cg_iteration<I, false>(h, z, g, L0);
       const int gp = it & 1;
       if (gap_on) CK(cudaEventRecord(h->gap_ev[gp][0], h->s));
-      if ((s = read_scal(h)) != MG_OK) return s;
-      if (gap_prev >= 0) {
+      if ((s = read_scal_issue(h, true)) != MG_OK) return s;
+      queued = it < p.maxit && rr_prev * ratio > tol2;
+      int gap_now = -1;  // pair completed in this iteration, read in the next (after its wait)
+      if (queued) {
+        if (gap_on) {
+          CK(cudaEventRecord(h->gap_ev[gp][1], h->s));
+          gap_now = gp;
+        }
+        if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
+      }
+      if ((s = read_scal_wait(h)) != MG_OK) return s;
+      if (gap_prev >= 0) {  // recorded in the previous iteration, so complete now
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, h->gap_ev[gap_prev][0], h->gap_ev[gap_prev][1]));
         h->t_ms[MG_K_HOST_GAP][0] += ms;
         h->t_n[MG_K_HOST_GAP][0] += 1;
-        gap_prev = -1;
       }
+      gap_prev = gap_now;
       sc = *h->hsc;
       if (sc.status & ST_TIMEOUT) {  // checked first: the blocks that gave up left their outputs unwritten
         result = fail(h, MG_ERR_DEVICE_TIMEOUT,
@@ -1543,16 +1580,20 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
       }
       rr = sc.rr;
       h->hist.push_back(std::sqrt(rr / bb));
+      ratio = rr_prev > 0 ? rr / rr_prev : 1.0;
+      rr_prev = rr;
       if (rr <= tol2) break;
       if (it == p.maxit) {
         result = fail(h, MG_ERR_NOT_CONVERGED, "maximum number of iterations reached");
         break;
       }
-      if (gap_on) {
-        CK(cudaEventRecord(h->gap_ev[gp][1], h->s));
-        gap_prev = gp;
+      if (!queued) {
+        if (gap_on) {
+          CK(cudaEventRecord(h->gap_ev[gp][1], h->s));
+          gap_prev = gp;
+        }
+        if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
       }
-      if ((s = run_precondition<I>(h, &z)) != MG_OK) return s;
     }
     if (it > p.maxit) it = p.maxit;
     // the last iteration's x += alpha p (deferred updates stop at exit)
@@ -2217,12 +2258,14 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
   mg_status s = MG_OK;
   if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_scal, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     s = fail(h, MG_ERR_CUDA, "stream or event creation failed");
   }
   if (s == MG_OK && (cudaMalloc(&h->dflag, sizeof(unsigned long long)) != cudaSuccess ||
-                     cudaMallocHost(&h->hsc, sizeof(Scal)) != cudaSuccess)) {
+                     cudaHostAlloc(&h->hsc, sizeof(Scal), cudaHostAllocMapped) != cudaSuccess ||
+                     cudaHostGetDevicePointer((void**)&h->hsc_dev, h->hsc, 0) != cudaSuccess)) {
     cudaGetLastError();
     s = fail(h, MG_ERR_ALLOC, "scalar buffers");
   }

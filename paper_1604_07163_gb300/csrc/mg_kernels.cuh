@@ -400,9 +400,12 @@ __device__ __forceinline__ void finish_apply(double a0, double a1, int mode, Sca
 }
 
 // Sums partials[0..n) (and partials[stride..stride+n)) in a fixed order and
-// updates the CG scalars.  One block of 256 threads.
+// updates the CG scalars.  One block of 256 threads.  With mirror (host
+// memory mapped into the device's address space) the updated scalars are
+// also written there, so that the host can read them after this kernel
+// without a copy queued on the stream.
 __global__ void __launch_bounds__(256) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
-                                                int flexible) {
+                                                int flexible, Scal* mirror) {
   pdl_wait();
   double a0 = 0.0, a1 = 0.0;
   for (int t = threadIdx.x; t < n; t += 256) {
@@ -410,7 +413,13 @@ __global__ void __launch_bounds__(256) k_finish(const double* partials, int n, i
     a1 += partials[stride + t];
   }
   block_sum2<256>(a0, a1);
-  if (threadIdx.x == 0) finish_apply(a0, a1, mode, s, flexible);
+  if (threadIdx.x == 0) {
+    finish_apply(a0, a1, mode, s, flexible);
+    if (mirror) {
+      *mirror = *s;
+      __threadfence_system();
+    }
+  }
 }
 
 // z-slab decomposition: one slab's reduction summed as k_finish sums it, into
