@@ -15,8 +15,11 @@ round trip, and the oracle timed on the host cores (a full solve, the second
 of two identical ones).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank solves its own independent problem (seed + rank):
-weak scaling, no collective on the data path.
+Under torchrun (N > 1) the ranks solve one problem together, decomposed into N
+z-slabs (rank r holds slab r; halo planes, dot-product sums and the
+agglomeration level travel over NCCL): strong scaling.  --replicas makes
+every rank solve its own independent problem instead (seed + rank, weak
+scaling, no collective on the data path).
 """
 from __future__ import annotations
 
@@ -151,7 +154,22 @@ def whole_job_dofs_per_s(unknowns_per_rank: int, world: int, ms_per_step: float)
     return world * unknowns_per_rank / (ms_per_step * 1e-3)
 
 
-def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised", slabs=1):
+L2_BYTES = 129e6
+
+
+def l2_note(N: int) -> str:
+    """How the timed steps avoid a warm L2: a float64 vector of N^3 points, the
+    solve's working set about 20 of them."""
+    vec = N ** 3 * 8
+    if vec > L2_BYTES:
+        return (f"no flush: inputs larger than L2 (each float64 vector {vec / 1e6:.0f} MB; "
+                f"working set > {20 * vec / 1e9:.1f} GB)")
+    return (f"warm L2: each float64 vector {vec / 1e6:.2f} MB, the whole working set stays in the "
+            f"129 MB L2 (a small parity-size case, not a throughput claim)")
+
+
+def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op="rediscretised", slabs=1,
+                decomposed=False, backend="nccl"):
     N = spec["N"]
     levels = 1
     M = N
@@ -164,9 +182,10 @@ def config_dict(spec, n_ranks, name=None, face_rule=0, adjoint=False, coarse_op=
                     f"edge k, {levels} levels ({'Galerkin R A P' if coarse_op == 'galerkin' else 're-discretised'} coarse "
                     f"operators), V(2,2) Chebyshev(2)-Jacobi, 3^3 dense Cholesky, CG to rel. residual "
                     f"{spec['rtol']:g}" + ("; step = forward + adjoint solve with the cell gradient" if adjoint else ""),
-        "l2": "no flush: inputs larger than L2 (each float64 vector 134 MB; working set > 2 GB)",
-        "parallelism": ("replicas" if n_ranks > 1 else "single GPU")
-                       + (f", solve decomposed into {slabs} z-slabs" if slabs > 1 else ""),
+        "l2": l2_note(N),
+        "parallelism": (f"one problem over {n_ranks} GPUs, one z-slab per rank ({backend})" if decomposed
+                        else ("replicas" if n_ranks > 1 else "single GPU")
+                        + (f", solve decomposed into {slabs} z-slabs" if slabs > 1 else "")),
     }
     return d
 
@@ -244,14 +263,17 @@ def run_ours(args):
     import paper_1604_07163_gb300 as mg
 
     rank, world, local = dist_env()
+    # ranks beyond the visible devices share them (only for checking the
+    # multi-rank path on fewer GPUs, with MG_BENCH_BACKEND=gloo: NCCL needs one
+    # device per rank)
+    dev = torch.device("cuda", local % max(torch.cuda.device_count(), 1) if world > 1 else 0)
+    torch.cuda.set_device(dev)
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
+        dist.init_process_group(os.environ.get("MG_BENCH_BACKEND", "nccl"))
     spec = dict(mi.WORKLOADS[args.workload])
-    seed = replica_seed(spec, rank)
+    decomposed = world > 1 and not args.replicas  # one problem over all ranks, one z-slab each
+    seed = spec["seed"] if decomposed else replica_seed(spec, rank)
     dims = (spec["N"],) * 3
     n = (spec["N"] - 2) ** 3
     k_np = mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed)
@@ -289,11 +311,24 @@ def run_ours(args):
     phi_obs = None
     if args.adjoint:  # loss 0.5 |phi - phi_obs|^2 with phi_obs from the k field of seed + 1
         kobs = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed + 1), device=dev)
-        So = mg.MGSolver(kobs, mg.Params(precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit,
-                                         coarse_op=args.coarse_op))
+        So = new_solver(kobs, precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit,
+                        coarse_op=args.coarse_op)
         phi_obs, _ = So.solve(f, rtol, raise_on_error=False)
         So.close()
         del So
+
+    def new_solver(kk, **kw):
+        """A solver of the run's parallel layout: in the decomposed run this
+        rank's slab of the z-slab decomposition, connected to the others."""
+        if decomposed:
+            kw.update(slabs=world, slab_rank=rank)
+        S = mg.MGSolver(kk, mg.Params(**kw))
+        if decomposed:
+            S.attach_transport()
+        return S
+
+    def dofs_per_s(ms):
+        return n / (ms * 1e-3) if decomposed else whole_job_dofs_per_s(n, world, ms)
 
     def step(S):
         x, st = S.solve(f, rtol, raise_on_error=False)
@@ -302,29 +337,34 @@ def run_ours(args):
         return x, st
 
     for form in (run_forms if not args.only_paper_configs else []):
-        S = mg.MGSolver(k, mg.Params(precision=form, maxit=args.maxit, face_rule=args.face_rule,
-                                     coarse_op=args.coarse_op, slabs=args.slabs))
+        S = new_solver(k, precision=form, maxit=args.maxit, face_rule=args.face_rule, coarse_op=args.coarse_op,
+                       **({} if decomposed else dict(slabs=args.slabs)))
         headline = form == HEADLINE
+        # per-kernel timing instruments the single-domain solve; the
+        # decomposed run's kernels are the same and are measured on one GPU
+        instrument = headline and not decomposed
         profile_all = None
         for w in range(args.warmup):
-            if headline and w == 0:
+            if instrument and w == 0:
                 S.timing(True)  # one fully instrumented warm-up solve: per-kernel breakdown
             step(S)
-            if headline and w == 0:
+            if instrument and w == 0:
                 profile_all = S.kernel_times()
                 S.timing(False)
         if headline:
-            dom = max(((c, v[0]) for (c, l), v in profile_all.items() if l == 0 and c != "host_gap"),
-                      key=lambda t: t[1])[0]
+            if instrument:
+                dom = max(((c, v[0]) for (c, l), v in profile_all.items() if l == 0 and c != "host_gap"),
+                          key=lambda t: t[1])[0]
             sampler = ClockSampler(dev.index if dev.index is not None else 0)
             sampler.start()
         ms, outs = timed(lambda: step(S), args.steps)
         x, st = outs[-1]
-        forms[form] = {"value": whole_job_dofs_per_s(n, world, ms), "ms_per_step": ms, "iters": st.iters,
+        forms[form] = {"value": dofs_per_s(ms), "ms_per_step": ms, "iters": st.iters,
                        "true_rel_resid": st.true_rel_resid, "status": st.status}
         solutions[form] = x.detach().clone()
         if headline:
             launches = sum(o[1].kernel_launches for o in outs)
+        if instrument:
             # the same K steps again with CUDA events around every launch of the
             # dominant finest-level kernel class and of the smoother steps (events
             # inside the V-cycle graph slow the whole solve, so the headline steps
@@ -340,7 +380,9 @@ def run_ours(args):
             ms_gap_run, gouts = timed(lambda: S.solve(f, rtol, raise_on_error=False), args.steps)
             gt = S.kernel_times().get(("host_gap", 0))
             S.timing(False)
+        if headline:
             clocks = sampler.stop()
+        if instrument:
             roofline = roofline_from(kt, form, clocks, dom, args.workload)
             smoother = roofline_from(kt, form, clocks, "cheb_step", args.workload)
             if gt:
@@ -352,6 +394,7 @@ def run_ours(args):
                                     "V-cycle replayed from its CUDA graph"}
             forms[form]["kernel_ms_per_solve_warmup_profile"] = {f"{c}@L{l}": round(v[0], 4)
                                                                   for (c, l), v in profile_all.items()}
+        if headline:
             # end to end through the C ABI with HOST buffers: the library copies the
             # pinned f in and x out inside every call
             x_host = torch.empty(dims, dtype=torch.float64).pin_memory()
@@ -365,7 +408,7 @@ def run_ours(args):
                 def e2e_step():
                     S.solve_host(f_host, x_host, rtol, raise_on_error=False)
             ms_e2e, _ = timed(e2e_step, args.steps)
-            e2e = {"value": whole_job_dofs_per_s(n, world, ms_e2e), "unit": "DOF/s",
+            e2e = {"value": dofs_per_s(ms_e2e), "unit": "DOF/s",
                    "h2d_bytes_per_step": f_host.numel() * 8, "d2h_bytes_per_step": x_host.numel() * 8,
                    "api": "mg_solve_host (C ABI, pinned host f and x)"}
         S.close()
@@ -390,7 +433,7 @@ def run_ours(args):
         return out
 
     slabs = None
-    if world == 1 and not args.adjoint and not args.no_slabs and args.slabs == 1:
+    if world == 1 and not args.adjoint and not args.no_slabs and args.slabs == 1 and not args.only_paper_configs:
         # the z-slab decomposition of the headline solve on this one GPU (slabs
         # run one after another, each halo exchange a device copy): its cost
         # over the single-domain solve and its distance from that solution
@@ -399,9 +442,9 @@ def run_ours(args):
             out_s = timed_variant(slabs=nsl, coarse_op=args.coarse_op)
             slabs[f"slabs{nsl}"] = out_s
     galerkin = paper = None
-    if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_galerkin:
+    if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_galerkin and not decomposed:
         galerkin = timed_variant(coarse_op="galerkin")
-    if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_paper_configs:
+    if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_paper_configs and not decomposed:
         # the solver configurations of the paper's experiments (Sec. 5): FGMRES
         # preconditioned by one V-cycle; Galerkin coarse operators with
         # Richardson(8)-Jacobi smoothing and the inexact coarsest GMRES-Jacobi
@@ -450,9 +493,12 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": forms[HEADLINE]["value"], "unit": "DOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms[HEADLINE]["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "higher_is_better": True, "scaling": "strong" if decomposed else "weak", "vs_baseline": None,
+        "dtype": "f32+f64",
         "data": "synthetic", "precision": HEADLINE, "iterations": forms[HEADLINE]["iters"],
-        "config": config_dict(spec, world, args.workload, args.face_rule, args.adjoint, args.coarse_op, args.slabs),
+        "config": config_dict(spec, world, args.workload, args.face_rule, args.adjoint, args.coarse_op,
+                              world if decomposed else args.slabs, decomposed,
+                              dist.get_backend() if world > 1 else "nccl"),
         "forms": forms, "speedup_mixed_vs_fp64": speedup, "target_513_c1e6": target,
         "galerkin_coarse_operators": galerkin, "paper_configurations": paper, "slab_decomposition": slabs,
         "roofline": roofline, "smoother_roofline": smoother, "host_gap": host_gap, "cpu_baseline": cpu,
@@ -528,15 +574,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 452.8 MB; step 1 with r.z: 604.5 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (528.7e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (399.6e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (395.9e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (82.4e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (68.6e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (792.1e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (551.3e6, "43150c3603489433"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (416.9e6, "43150c3603489433"),
+    # 450.0 MB; step 1 with r.z: 601.6 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (525.8e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.6e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.3e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (80.1e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.8e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.6e6, "182bdf6e7d0704dd"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.5e6, "182bdf6e7d0704dd"),
 }
 
 
@@ -625,6 +671,8 @@ def main():
                     help="skip the 513^3 contrast-10^6 Galerkin target solve")
     ap.add_argument("--only-paper-configs", action="store_true",
                     help="time only the Galerkin variant and the paper's solver configurations (for profiling)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: every rank solves its own problem instead of one decomposed problem")
     ap.add_argument("--slabs", type=int, default=1,
                     help="solve every form with the z-slab decomposition into this many slabs (1: none)")
     ap.add_argument("--no-slabs", action="store_true",

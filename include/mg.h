@@ -157,6 +157,13 @@ typedef struct {
                           whole grid */
   int slab_level;      /* agglomeration level of the slabs: 0 (default) the bottom kernel's first level;
                           otherwise that level, at most the bottom kernel's first level, at least 1 */
+  int slab_rank;       /* -1 (default): this process holds all slabs.  0..slabs-1: this process holds only
+                          slab slab_rank (one process per rank of a distributed run) and exchanges halo
+                          planes, dot-product sums and the agglomeration level with the other ranks through
+                          the transport given to mg_set_transport; every rank gathers the agglomeration level
+                          and runs the whole-grid V-cycle from there itself.  mg_solve then reads all of f and
+                          writes only this slab's planes of x (the first and last rank also the boundary
+                          planes); statistics are those of the whole solve on every rank */
 } mg_params;
 
 typedef struct {
@@ -192,6 +199,36 @@ mg_status mg_setup(mg_handle** h, int Nx, int Ny, int Nz, const double* k_cells,
  * plane), so restriction needs one halo plane above a slab and prolongation
  * one below.  MG_ERR_ARG when the grid, the parameters or cap do not allow it. */
 mg_status mg_slab_plan(int Nx, int Ny, int Nz, const mg_params* p, int* bounds, int cap, int* agglomerate_level);
+
+/* Transport between the ranks of a z-slab solve (mg_params.slab_rank >= 0).
+ * The caller allocates the device buffers (sizes from
+ * mg_slab_transport_sizes) and implements three collective operations over
+ * the ranks 0..slabs-1; each is called by every rank in the same order,
+ * with the library's stream, and must complete the transfer before the
+ * stream's next work (enqueue it on that stream, or finish it before
+ * returning).  Every call returns 0 on success.
+ *  exchange(ctx, nbytes, has_lo, has_hi, stream): the first nbytes of
+ *    send_lo go to rank-1 (into its recv_hi) and of send_hi to rank+1 (into
+ *    its recv_lo); recv_lo receives from rank-1 and recv_hi from rank+1.
+ *    has_lo / has_hi say whether those neighbours exist.
+ *  allreduce(ctx, n, stream): reduce_buf[0..n) becomes its sum over the ranks.
+ *  allgather(ctx, block_bytes, stream): gather_recv[r*block_bytes ..) becomes
+ *    rank r's gather_send[0 .. block_bytes) for every r. */
+typedef struct {
+  void* ctx;
+  int (*exchange)(void* ctx, long long nbytes, int has_lo, int has_hi, void* stream);
+  int (*allreduce)(void* ctx, int n, void* stream);
+  int (*allgather)(void* ctx, long long block_bytes, void* stream);
+  void *send_lo, *send_hi, *recv_lo, *recv_hi; /* device, plane_bytes each */
+  double* reduce_buf;                           /* device, 2 doubles */
+  void *gather_send, *gather_recv;              /* device, block_bytes and slabs * block_bytes */
+} mg_transport;
+
+/* Buffer sizes of a rank's transport: the largest halo plane and the
+ * agglomeration level's largest block of planes, in bytes. */
+mg_status mg_slab_transport_sizes(const mg_handle* h, long long* plane_bytes, long long* block_bytes);
+/* Set (copy) the transport of a handle built with slab_rank >= 0. */
+mg_status mg_set_transport(mg_handle* h, const mg_transport* t);
 
 /* Change the stream subsequent calls enqueue on. */
 mg_status mg_set_stream(mg_handle* h, void* stream);

@@ -21,7 +21,8 @@ EXPORTS = [
     "mg_params_default", "mg_setup", "mg_set_stream", "mg_solve", "mg_solve_adjoint", "mg_free", "mg_last_error",
     "mg_num_levels", "mg_level_dims", "mg_level_interval", "mg_history", "mg_apply", "mg_smooth", "mg_residual_restrict",
     "mg_prolong_add", "mg_coarse_solve", "mg_vcycle", "mg_gradient", "mg_residual_norm", "mg_timing_enable",
-    "mg_timing_read", "mg_residual_norm_noalloc", "mg_solve_host", "mg_slab_plan",
+    "mg_timing_read", "mg_residual_norm_noalloc", "mg_solve_host", "mg_slab_plan", "mg_slab_transport_sizes",
+    "mg_set_transport",
 ]
 KERNEL_CLASSES = ["cheb_zero", "cheb_step", "resid", "restrict", "prolong", "bottom", "cg_dir", "cg_upd", "dot",
                   "cast", "cg_apply", "host_gap"]
@@ -38,6 +39,20 @@ class MgParams(C.Structure):
         ("krylov", C.c_int), ("gmres_restart", C.c_int), ("eig_mode", C.c_int), ("eig_safety", C.c_double),
         ("coarse_solve", C.c_int), ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int),
         ("bottom_blocks", C.c_int), ("test_inject", C.c_int), ("slabs", C.c_int), ("slab_level", C.c_int),
+        ("slab_rank", C.c_int),
+    ]
+
+
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_void_p)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_void_p)
+ALLGATHER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_longlong, C.c_void_p)
+
+
+class MgTransport(C.Structure):
+    _fields_ = [
+        ("ctx", C.c_void_p), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN), ("allgather", ALLGATHER_FN),
+        ("send_lo", C.c_void_p), ("send_hi", C.c_void_p), ("recv_lo", C.c_void_p), ("recv_hi", C.c_void_p),
+        ("reduce_buf", C.c_void_p), ("gather_send", C.c_void_p), ("gather_recv", C.c_void_p),
     ]
 
 
@@ -75,6 +90,8 @@ def load():
         "mg_solve": ([vp, vp, vp, d, P(MgStats)], i),
         "mg_solve_host": ([vp, vp, vp, d, P(MgStats)], i),
         "mg_slab_plan": ([i, i, i, P(MgParams), P(C.c_int), i, P(C.c_int)], i),
+        "mg_slab_transport_sizes": ([vp, P(C.c_longlong), P(C.c_longlong)], i),
+        "mg_set_transport": ([vp, P(MgTransport)], i),
         "mg_solve_adjoint": ([vp, vp, vp, d, vp, vp, P(MgStats)], i),
         "mg_free": ([vp], i),
         "mg_last_error": ([vp], C.c_char_p),

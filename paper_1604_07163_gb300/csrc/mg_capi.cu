@@ -142,6 +142,10 @@ struct mg_handle {
   i64 lin_lo = 0, lin_hi = -1;
   bool sub = false;                    // a slab sub-hierarchy (stream and scalars are the parent's)
   int nslab = 1, la = 0;               // parent: slabs and agglomeration level
+  int slab_first = 0;                  // parent: global index of its first (in rank mode: only) slab
+  bool rank_mode = false;              // parent: holds one slab and talks to the other ranks through tr
+  mg_transport tr{};
+  bool tr_set = false;
   std::vector<mg_handle*> slab;        // parent: the slab sub-hierarchies
   std::vector<int> slab_z0;            // parent: first interior plane of slab s on level l at l*(nslab+1)+s
   double* slots = nullptr;             // parent: per-slab reduction slots (2 x nslab)
@@ -1496,6 +1500,8 @@ mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
   return MG_OK;
 }
 
+constexpr double QUEUE_MARGIN = 8.0;  // on the squared residual norm
+
 template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
   using TV = typename I::TVt;
   auto t0 = clk::now();
@@ -1536,9 +1542,12 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
     int gap_prev = -1;  // event pair recorded in the previous iteration, read after the next host sync
     // The next V-cycle needs only the residual this iteration writes, so it is
     // queued behind the copy of the CG scalars before the host waits for
-    // them: the host's convergence test then overlaps the device's work.  It
-    // is skipped when the last residual reduction predicts convergence in this
-    // iteration (a V-cycle queued after the last iteration would be wasted).
+    // them: the host's convergence test then overlaps the device's work.  A
+    // V-cycle queued after the last iteration is wasted (about 1% of a solve),
+    // so queueing stops once the last residual reduction predicts a residual
+    // within a factor QUEUE_MARGIN of the tolerance (CG's reduction varies
+    // from one iteration to the next; the margin stops it a few iterations
+    // before the end, each of which then waits for the host, about 10 us).
     double rr_prev = rr, ratio = 1.0;
     bool queued = false;  // the next V-cycle is already queued
     for (it = 1; it <= p.maxit; ++it) {
@@ -1547,7 +1556,7 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
       const int gp = it & 1;
       if (gap_on) CK(cudaEventRecord(h->gap_ev[gp][0], h->s));
       if ((s = read_scal_issue(h, true)) != MG_OK) return s;
-      queued = it < p.maxit && rr_prev * ratio > tol2;
+      queued = it < p.maxit && rr_prev * ratio > QUEUE_MARGIN * tol2;
       int gap_now = -1;  // pair completed in this iteration, read in the next (after its wait)
       if (queued) {
         if (gap_on) {
@@ -1659,10 +1668,13 @@ mg_status build_slabs(mg_handle* h) {
   }
   h->nslab = S;
   h->la = la;
+  h->rank_mode = p.slab_rank >= 0;
+  h->slab_first = h->rank_mode ? p.slab_rank : 0;
   AL(h->slots, double, 2 * (i64)S);
   const size_t vb = vbytes(h), cb = cbytes(h);
   const bool mixed = p.precision != MG_FP64;
-  for (int s = 0; s < S; ++s) {
+  const int s_end = h->rank_mode ? h->slab_first + 1 : S;
+  for (int s = h->slab_first; s < s_end; ++s) {
     mg_handle* c = new (std::nothrow) mg_handle();
     if (!c) return fail(h, MG_ERR_ALLOC, "host allocation failed");
     h->slab.push_back(c);
@@ -1778,6 +1790,26 @@ mg_status build_slabs(mg_handle* h) {
 // planes into each other's pad planes (a slab's last plane to the next slab's
 // lower pad plane, the next slab's first plane to its upper pad plane).
 mg_status slab_exchange(mg_handle* h, const std::vector<std::vector<Pass>>& R, size_t i) {
+  if (h->rank_mode) {  // the one local slab swaps planes with the neighbouring ranks
+    const Pass& a = R[0][i];
+    const size_t es = (size_t)a.halo_bytes, pb = (size_t)a.halo_g.sz * es;
+    char* A = (char*)a.halo;
+    const Geom& ga = a.halo_g;
+    const int r = h->slab_first;
+    const int lo = r > 0, hi = r + 1 < h->nslab;
+    if (lo) CK(cudaMemcpyAsync(h->tr.send_lo, A + (size_t)ga.off * es, pb, cudaMemcpyDeviceToDevice, h->s));
+    if (hi)
+      CK(cudaMemcpyAsync(h->tr.send_hi, A + (size_t)(ga.off + (i64)(ga.nz - 1) * ga.sz) * es, pb,
+                         cudaMemcpyDeviceToDevice, h->s));
+    CKL();
+    if (h->tr.exchange(h->tr.ctx, (long long)pb, lo, hi, (void*)h->s) != 0)
+      return fail(h, MG_ERR_CUDA, "slab transport: halo exchange failed");
+    if (lo) CK(cudaMemcpyAsync(A + (size_t)(ga.off - ga.sz) * es, h->tr.recv_lo, pb, cudaMemcpyDeviceToDevice, h->s));
+    if (hi)
+      CK(cudaMemcpyAsync(A + (size_t)(ga.off + (i64)ga.nz * ga.sz) * es, h->tr.recv_hi, pb, cudaMemcpyDeviceToDevice,
+                         h->s));
+    return MG_OK;
+  }
   for (int s = 0; s + 1 < h->nslab; ++s) {
     const Pass& a = R[s][i];
     const Pass& b = R[s + 1][i];
@@ -1795,13 +1827,32 @@ mg_status slab_exchange(mg_handle* h, const std::vector<std::vector<Pass>>& R, s
 
 // A reduction finished across the slabs: each slab's block sums into its
 // slot, then the slots added in slab order and the CG scalars updated.
-void slab_finish(mg_handle* h, const int* nbs, int mode) {
+mg_status slab_finish(mg_handle* h, const int* nbs, int mode) {
   const int S = h->nslab;
+  if (h->rank_mode) {  // this rank's sums, summed over the ranks by the transport
+    launch(h, k_finish_partial, dim3(1), dim3(256), 0, (const double*)h->slab[0]->partials, nbs[0],
+           h->slab[0]->pstride, h->tr.reduce_buf, 1);
+    CKL();
+    if (h->tr.allreduce(h->tr.ctx, 2, (void*)h->s) != 0) return fail(h, MG_ERR_CUDA, "slab transport: all-reduce failed");
+    launch(h, k_combine, dim3(1), dim3(32), 0, (const double*)h->tr.reduce_buf, 1, mode, h->dsc, h->prm.flexible);
+    h->launches += 2;
+    return MG_OK;
+  }
   for (int s = 0; s < S; ++s)
     launch(h, k_finish_partial, dim3(1), dim3(256), 0, (const double*)h->slab[s]->partials, nbs[s],
            h->slab[s]->pstride, h->slots + s, S);
   launch(h, k_combine, dim3(1), dim3(32), 0, (const double*)h->slots, S, mode, h->dsc, h->prm.flexible);
   h->launches += S + 1;
+  return MG_OK;
+}
+
+// Bytes of the agglomeration level's largest slab block (rank mode).
+i64 slab_block_bytes(const mg_handle* h) {
+  const int S = h->nslab;
+  int mz = 0;
+  for (int s = 0; s < S; ++s)
+    mz = std::max(mz, h->slab_z0[(size_t)h->la * (S + 1) + s + 1] - h->slab_z0[(size_t)h->la * (S + 1) + s]);
+  return (i64)mz * h->lv[h->la].g.sz * (i64)vbytes(h);
 }
 
 // The agglomeration level: gather the slabs' right-hand sides into the root
@@ -1812,6 +1863,26 @@ template <class I> mg_status slab_agglomerate(mg_handle* h, int la) {
   const int S = h->nslab;
   LevelBuf& R = h->lv[la];
   const i64 sz = R.g.sz;
+  if (h->rank_mode) {  // every rank gathers all blocks and runs the whole-grid V-cycle itself
+    const LevelBuf& C = h->slab[0]->lv[la];
+    const i64 bb = slab_block_bytes(h);
+    CK(cudaMemcpyAsync(h->tr.gather_send, (const TV*)C.b + C.g.off, (size_t)C.g.nz * sz * sizeof(TV),
+                       cudaMemcpyDeviceToDevice, h->s));
+    CKL();
+    if (h->tr.allgather(h->tr.ctx, (long long)bb, (void*)h->s) != 0)
+      return fail(h, MG_ERR_CUDA, "slab transport: all-gather failed");
+    for (int q = 0; q < S; ++q) {
+      const int z0 = h->slab_z0[(size_t)la * (S + 1) + q], z1 = h->slab_z0[(size_t)la * (S + 1) + q + 1];
+      CK(cudaMemcpyAsync((TV*)R.b + R.g.off + (i64)z0 * sz, (const char*)h->tr.gather_recv + (size_t)q * bb,
+                         (size_t)(z1 - z0) * sz * sizeof(TV), cudaMemcpyDeviceToDevice, h->s));
+    }
+    const int cur = I::vcycle(h, la);
+    LevelBuf& M = h->slab[0]->lv[la];
+    const int z0 = h->slab_z0[(size_t)la * (S + 1) + h->slab_first];
+    CK(cudaMemcpyAsync((TV*)M.x[0] + M.g.off - sz, (const TV*)R.x[cur] + R.g.off + (i64)(z0 - 1) * sz,
+                       (size_t)(M.g.nz + 2) * sz * sizeof(TV), cudaMemcpyDeviceToDevice, h->s));
+    return MG_OK;
+  }
   for (int s = 0; s < S; ++s) {
     const LevelBuf& C = h->slab[s]->lv[la];
     const int z0 = h->slab_z0[(size_t)la * (S + 1) + s];
@@ -1830,7 +1901,7 @@ template <class I> mg_status slab_agglomerate(mg_handle* h, int la) {
 
 // Replays a recorded phase on all slabs, pass by pass.
 template <class I> mg_status slab_replay(mg_handle* h, const std::vector<std::vector<Pass>>& R) {
-  const int S = h->nslab;
+  const int S = (int)h->slab.size();  // the slabs this process holds
   std::vector<int> nbs(S);
   mg_status st;
   for (size_t i = 0; i < R[0].size(); ++i) {
@@ -1846,7 +1917,7 @@ template <class I> mg_status slab_replay(mg_handle* h, const std::vector<std::ve
         break;
       case Pass::FINISH:
         for (int s = 0; s < S; ++s) nbs[s] = R[s][i].nb;
-        slab_finish(h, nbs.data(), p0.mode);
+        if ((st = slab_finish(h, nbs.data(), p0.mode)) != MG_OK) return st;
         break;
       case Pass::AGGLOM:
         if ((st = slab_agglomerate<I>(h, p0.level)) != MG_OK) return st;
@@ -1861,7 +1932,7 @@ template <class I> mg_status slab_replay(mg_handle* h, const std::vector<std::ve
 template <class I, bool FLEX> mg_status slab_record(mg_handle* h) {
   using TV = typename I::TVt;
   if (!h->vrec.empty()) return MG_OK;
-  const int S = h->nslab;
+  const int S = (int)h->slab.size();
   h->vrec.assign(S, {});
   h->crec.assign(S, {});
   h->vz.assign(S, nullptr);
@@ -1888,25 +1959,27 @@ template <class I, bool FLEX> mg_status slab_record(mg_handle* h) {
 template <class I> mg_status slab_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
   auto t0 = clk::now();
   const mg_params& p = h->prm;
-  const int S = h->nslab;
+  const int S = (int)h->slab.size();  // the slabs this process holds
+  const int gs0 = h->slab_first;      // global index of the first of them
   const Geom& gG = h->lv[0].g;
   const i64 plane = (i64)(gG.nx + 2) * (gG.ny + 2);  // elements per dense full-grid plane
   h->hist.clear();
   const long long launches0 = h->launches;
   mg_status s;
+  if (h->rank_mode && !h->tr_set) return fail(h, MG_ERR_ARG, "slab_rank >= 0 needs a transport (mg_set_transport)");
   if ((s = p.flexible ? slab_record<I, true>(h) : slab_record<I, false>(h)) != MG_OK) return s;
   std::vector<int> nbs(S);
   CK(cudaMemsetAsync(h->dsc, 0, sizeof(Scal), h->s));
   for (int q = 0; q < S; ++q) {
     mg_handle* c = h->slab[q];
     const Geom& g = c->lv[0].g;
-    k_pack<double><<<lin_blocks(h, g.npts()), 256, 0, h->s>>>(f + (i64)h->slab_z0[q] * plane, c->cb, g);
+    k_pack<double><<<lin_blocks(h, g.npts()), 256, 0, h->s>>>(f + (i64)h->slab_z0[gs0 + q] * plane, c->cb, g);
     CK(cudaMemsetAsync(c->cx, 0, (size_t)g.len * 8, h->s));
     CK(cudaMemsetAsync(c->cp, 0, (size_t)g.len * 8, h->s));
     CK(cudaMemcpyAsync(c->cr, c->cb, (size_t)g.len * 8, cudaMemcpyDeviceToDevice, h->s));
     nbs[q] = linear<true>(c, g.len, LinDot<double>{c->cb, c->cb});
   }
-  slab_finish(h, nbs.data(), FIN_BB);
+  if ((s = slab_finish(h, nbs.data(), FIN_BB)) != MG_OK) return s;
   if ((s = read_scal(h)) != MG_OK) return s;
   Scal sc = *h->hsc;
   mg_status result = MG_OK;
@@ -1950,9 +2023,10 @@ template <class I> mg_status slab_solve(mg_handle* h, const double* f, double* x
   for (int q = 0; q < S; ++q) {
     mg_handle* c = h->slab[q];
     const Geom& g = c->lv[0].g;
-    const int kf = q == 0 ? 0 : 1, kl = q == S - 1 ? g.nz + 1 : g.nz;
+    const int gq = gs0 + q;
+    const int kf = gq == 0 ? 0 : 1, kl = gq == h->nslab - 1 ? g.nz + 1 : g.nz;
     k_unpack<double><<<lin_blocks(h, (i64)(g.nx + 2) * (g.ny + 2) * (kl - kf + 1)), 256, 0, h->s>>>(
-        c->cx, x + (i64)h->slab_z0[q] * plane, g, kf, kl);
+        c->cx, x + (i64)h->slab_z0[gq] * plane, g, kf, kl);
   }
   // true residual in float64: halo exchange of x, residual and its norm per slab
   {
@@ -1969,7 +2043,7 @@ template <class I> mg_status slab_solve(mg_handle* h, const double* f, double* x
       OpResidual<double, double, double, double> res{c->cx, c->cb, c->cq, C0.kx64, C0.ky64, C0.kz64};
       nbs[q] = zmarch<true>(c, C0.g, res);
     }
-    slab_finish(h, nbs.data(), FIN_TRUE);
+    if ((s = slab_finish(h, nbs.data(), FIN_TRUE)) != MG_OK) return s;
   }
   if ((s = read_scal(h)) != MG_OK) return s;
   h->st.iters = it;
@@ -2216,6 +2290,7 @@ mg_status mg_params_default(mg_params* p) {
   p->test_inject = 0;
   p->slabs = 1;
   p->slab_level = 0;
+  p->slab_rank = -1;
   return MG_OK;
 }
 
@@ -2237,7 +2312,8 @@ mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cell
       p.krylov > MG_KRYLOV_FGMRES || p.gmres_restart < 1 || p.gmres_restart > 256 || p.eig_mode < 0 ||
       p.eig_mode > 1 || !(p.eig_safety > 0.0) || p.coarse_solve < 0 || p.coarse_solve > 1 ||
       !(p.coarse_rtol > 0.0) || p.coarse_maxit < 1 || p.coarse_maxit > 32 || (p.bottom_blocks != 0 && p.bottom_blocks != 1 && p.bottom_blocks != 2 && p.bottom_blocks != 4 && p.bottom_blocks != 8) ||
-      p.test_inject < 0 || p.test_inject > 3 || p.slabs < 1 || p.slabs > MG_MAX_SLABS || p.slab_level < 0 ||
+      p.test_inject < 0 || p.test_inject > 3 || p.slabs < 1 || p.slabs > MG_MAX_SLABS || p.slab_level < 0 || p.slab_rank < -1 ||
+      p.slab_rank >= p.slabs || (p.slab_rank >= 0 && p.slabs < 2) ||
       (p.slabs > 1 && (p.krylov != MG_KRYLOV_CG || p.stencil_kernel == 1 || p.nonzero_guess)))
     return fail(nullptr, MG_ERR_ARG, "invalid mg_params");
   // Fletcher-Reeves by default: measured on GB300 the float32 / bfloat16
@@ -2297,6 +2373,25 @@ mg_status mg_solve(mg_handle* h, const double* f, double* x, double rtol, mg_sta
   if (h->prm.krylov == MG_KRYLOV_FGMRES)
     return dispatch(h, [&](auto impl) { return fgmres_impl<decltype(impl)>(h, f, x, rtol, st); });
   return dispatch(h, [&](auto impl) { return solve_impl<decltype(impl)>(h, f, x, rtol, st); });
+}
+
+mg_status mg_slab_transport_sizes(const mg_handle* h, long long* plane_bytes, long long* block_bytes) {
+  if (!h || !plane_bytes || !block_bytes || !h->rank_mode) return MG_ERR_ARG;
+  i64 pb = 0;
+  for (int l = 0; l <= h->la; ++l)
+    pb = std::max(pb, h->lv[l].g.sz * (i64)(l == 0 ? 8 : (i64)vbytes(h)));  // level 0 also exchanges float64 CG vectors
+  *plane_bytes = pb;
+  *block_bytes = slab_block_bytes(h);
+  return MG_OK;
+}
+
+mg_status mg_set_transport(mg_handle* h, const mg_transport* t) {
+  if (!h || !t || !h->rank_mode || !t->exchange || !t->allreduce || !t->allgather || !t->send_lo || !t->send_hi ||
+      !t->recv_lo || !t->recv_hi || !t->reduce_buf || !t->gather_send || !t->gather_recv)
+    return h ? fail(h, MG_ERR_ARG, "invalid transport (or the handle holds all slabs)") : MG_ERR_ARG;
+  h->tr = *t;
+  h->tr_set = true;
+  return MG_OK;
 }
 
 mg_status mg_slab_plan(int Nx, int Ny, int Nz, const mg_params* p, int* bounds, int cap, int* agglomerate_level) {

@@ -47,6 +47,7 @@ class Params:
     test_inject: int = 0  # test only: 1 negated outer diagonal (breakdown), 2 negated coarsest diagonal (not SPD)
     slabs: int = 1  # z-slab decomposition of the solve (1: none)
     slab_level: int = 0  # agglomeration level of the slabs (0: the bottom kernel's first level)
+    slab_rank: int = -1  # -1: this process holds all slabs; r: only slab r (one rank of a distributed solve)
 
     def to_c(self, k_is_log: bool) -> L.MgParams:
         p = L.MgParams()
@@ -68,6 +69,7 @@ class Params:
         p.test_inject = self.test_inject
         p.slabs = self.slabs
         p.slab_level = self.slab_level
+        p.slab_rank = self.slab_rank
         p.precision = L.PRECISION[self.precision]
         p.k_is_log = 1 if k_is_log else 0
         return p
@@ -120,6 +122,13 @@ class MGSolver:
         if rc != L.MG_OK:
             raise L.MgError(rc, self._lib.mg_last_error(None).decode())
         self._h = h
+
+    def attach_transport(self, group=None):
+        """For a handle built with slab_rank >= 0: connect it to the other
+        ranks of the torch.distributed group (see slab_transport)."""
+        from .slab_transport import SlabTransport
+        self._transport = SlabTransport(self, group)
+        return self._transport
 
     def close(self):
         if self._h is not None:
