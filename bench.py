@@ -336,7 +336,7 @@ def run_ours(args):
             S.solve_adjoint((x - phi_obs).contiguous(), rtol, x)
         return x, st
 
-    for form in (run_forms if not args.only_paper_configs else []):
+    for form in (run_forms if not (args.only_paper_configs or args.only) else []):
         S = new_solver(k, precision=form, maxit=args.maxit, face_rule=args.face_rule, coarse_op=args.coarse_op,
                        **({} if decomposed else dict(slabs=args.slabs)))
         headline = form == HEADLINE
@@ -432,6 +432,13 @@ def run_ours(args):
         del S
         return out
 
+    if args.only:
+        out_v = timed_variant(**VARIANTS[args.only])
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": "DOF/s", "variant": args.only, "result": out_v,
+                              "config": config_dict(spec, world, args.workload)}), flush=True)
+        return
+
     slabs = None
     if world == 1 and not args.adjoint and not args.no_slabs and args.slabs == 1 and not args.only_paper_configs:
         # the z-slab decomposition of the headline solve on this one GPU (slabs
@@ -443,7 +450,7 @@ def run_ours(args):
             slabs[f"slabs{nsl}"] = out_s
     galerkin = paper = None
     if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_galerkin and not decomposed:
-        galerkin = timed_variant(coarse_op="galerkin")
+        galerkin = timed_variant(**VARIANTS["galerkin"])
     if args.coarse_op == "rediscretised" and not args.adjoint and not args.no_paper_configs and not decomposed:
         # the solver configurations of the paper's experiments (Sec. 5): FGMRES
         # preconditioned by one V-cycle; Galerkin coarse operators with
@@ -451,12 +458,8 @@ def run_ours(args):
         # solve to 1e-4 (the truncation runs); re-discretised coarse operators
         # with Chebyshev(10)-Jacobi smoothing (the comparison runs, here with the
         # exact coarsest solve in place of their block-Jacobi/ILU(0) one)
-        paper = {
-            "fgmres_galerkin_richardson8_gmres_coarse": timed_variant(
-                krylov="fgmres", coarse_op="galerkin", smoother="richardson", nu_pre=8, nu_post=8,
-                coarse_solve="gmres", coarse_rtol=1e-4),
-            "fgmres_rediscretised_chebyshev10": timed_variant(krylov="fgmres", cheby_degree=10),
-        }
+        paper = {name: timed_variant(**VARIANTS[name])
+                 for name in ("fgmres_galerkin_richardson8_gmres_coarse", "fgmres_rediscretised_chebyshev10")}
     if args.only_paper_configs:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": "DOF/s", "galerkin_coarse_operators": galerkin,
@@ -562,6 +565,15 @@ def target_513_c1e6(args, dev, timed):
 
 # float64 operations per point of the float64-pipe-bound outer-CG kernel
 # (6 FMA for the neighbour sum, 1 for D p - S, 1 for p.q)
+# Method variants timed beside the headline solve (same problem, precision and
+# tolerance): Galerkin coarse operators, and the two solver configurations of
+# the paper's Sec. 5 experiments.
+VARIANTS = {
+    "galerkin": dict(coarse_op="galerkin"),
+    "fgmres_galerkin_richardson8_gmres_coarse": dict(krylov="fgmres", coarse_op="galerkin", smoother="richardson",
+                                                     nu_pre=8, nu_post=8, coarse_solve="gmres", coarse_rtol=1e-4),
+    "fgmres_rediscretised_chebyshev10": dict(krylov="fgmres", cheby_degree=10),
+}
 CG_APPLY_FLOPS = 16
 # GB300: 152 SMs x 2 float64 FMA per clock per SM (the nominal 1.25 TFLOP/s at 2.07 GHz)
 FP64_FLOP_PER_SM_CLK = 4
@@ -574,15 +586,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 450.0 MB; step 1 with r.z: 601.6 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (525.8e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.6e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.3e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (80.1e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.8e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.6e6, "182bdf6e7d0704dd"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.5e6, "182bdf6e7d0704dd"),
+    # 450.0 MB; step 1 with r.z: 601.8 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (525.9e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (397.0e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.1e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.1e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.8e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.6e6, "e5f635a3b2110a17"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.7e6, "e5f635a3b2110a17"),
 }
 
 
@@ -671,6 +683,8 @@ def main():
                     help="skip the 513^3 contrast-10^6 Galerkin target solve")
     ap.add_argument("--only-paper-configs", action="store_true",
                     help="time only the Galerkin variant and the paper's solver configurations (for profiling)")
+    ap.add_argument("--only", choices=sorted(VARIANTS),
+                    help="time only this one method variant of the headline precision (for profiling)")
     ap.add_argument("--replicas", action="store_true",
                     help="under torchrun: every rank solves its own problem instead of one decomposed problem")
     ap.add_argument("--slabs", type=int, default=1,
