@@ -1202,14 +1202,16 @@ mg_status build_hierarchy(mg_handle* h, int Nx, int Ny, int Nz, const double* k,
   const Geom& gc = h->lv[L - 1].g;
   h->nc = (int)gc.npts();
   // In float64 the bottom kernel's passes are bound by the float64 pipe of
-  // its SM: a finest bottom level of more than one point per thread spreads
-  // over a cluster of up to 8 blocks (8 SMs).  The float32 passes are bound
+  // its SM, and 27-point (Galerkin) passes by the work of one SM: a finest
+  // bottom level of more than one point per thread then spreads over a
+  // cluster of up to 8 blocks (8 SMs).  The float32 7-point passes are bound
   // by latency and barriers, which a cluster barrier does not improve
-  // (measured on GB300: one block is as fast as 4 or 8, faster than 2).
+  // (measured on GB300 at 257^3: 7-point float32, one block is as fast as 4
+  // or 8; 27-point float32, 4 blocks take the solve from 35.6 to 35.2 ms).
   {
     const i64 n0 = h->lv[h->lb].g.npts();
     int nb = 1;
-    if (p.precision == MG_FP64)
+    if (p.precision == MG_FP64 || (p.coarse_op == MG_COARSE_GALERKIN && h->lb >= 1))
       while (nb < 8 && n0 > (i64)nb * BOT_THREADS) nb *= 2;
     if (p.bottom_blocks > 0) nb = p.bottom_blocks;
     if (nb > 1 && !dispatch(h, [&](auto impl) { return decltype(impl)::bottom_cluster_fits(nb); })) nb = 1;
