@@ -289,18 +289,26 @@ def run_ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def timed(fn, steps):
+    step_medians = {}
+
+    def timed(fn, steps, key=None):
         """Device time of `steps` calls of fn (CUDA events on the current
         stream, barrier and synchronize on both sides), max over ranks, ms
-        per call."""
+        per call.  An event between consecutive calls also gives each call's
+        own time; with key, their median (max over ranks) is kept in
+        step_medians[key]."""
         barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        out = [fn() for _ in range(steps)]
-        e1.record()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record()
+        out = []
+        for i in range(steps):
+            out.append(fn())
+            ev[i + 1].record()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1), dev) / steps, out
+        if key is not None:
+            per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
+            step_medians[key] = max_over_ranks(per[len(per) // 2], dev)
+        return max_over_ranks(ev[0].elapsed_time(ev[steps]), dev) / steps, out
 
     forms = {}
     solutions = {}
@@ -357,10 +365,10 @@ def run_ours(args):
                           key=lambda t: t[1])[0]
             sampler = ClockSampler(dev.index if dev.index is not None else 0)
             sampler.start()
-        ms, outs = timed(lambda: step(S), args.steps)
+        ms, outs = timed(lambda: step(S), args.steps, key=form)
         x, st = outs[-1]
-        forms[form] = {"value": dofs_per_s(ms), "ms_per_step": ms, "iters": st.iters,
-                       "true_rel_resid": st.true_rel_resid, "status": st.status}
+        forms[form] = {"value": dofs_per_s(ms), "ms_per_step": ms, "ms_per_step_median": step_medians[form],
+                       "iters": st.iters, "true_rel_resid": st.true_rel_resid, "status": st.status}
         solutions[form] = x.detach().clone()
         if headline:
             launches = sum(o[1].kernel_launches for o in outs)

@@ -3,6 +3,7 @@
 // launch geometry, the V-cycle driver (Algorithm 1 applied recursively),
 // the float64 PCG loop and the step entry points.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -53,6 +54,17 @@ struct LevelBuf {
 };
 
 std::string g_setup_error;
+
+// Named host ranges for profilers (ncu --nvtx, Nsight Systems): setup, each
+// solve, each outer iteration and each V-cycle.  The NVTX v3 header is
+// self-contained; with no tool attached a range costs one check of a
+// function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // One step of a recorded solve phase of a z-slab sub-hierarchy (see the
 // z-slab decomposition below): a kernel launch (with the operand whose halo
@@ -1435,6 +1447,7 @@ constexpr int VCYCLE_CLASSES = (1 << MG_K_CHEB_ZERO) | (1 << MG_K_CHEB_STEP) | (
 // CUDA graph captured on first use when the handle enables graphs.
 
 template <class I, class TV> mg_status run_precondition(mg_handle* h, TV** z) {
+  NvtxRange range("mg V-cycle");
   if (!h->prm.use_graph || (h->timing && (h->t_cls_mask & VCYCLE_CLASSES))) {  // timed launches run eagerly
     *z = I::precondition(h);
     CKL();
@@ -1490,6 +1503,7 @@ struct Guard {
 
 template <class I, bool FLEX, class TV>
 mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
+  NvtxRange range("mg CG iteration");
   // x += alpha_prev p, p = z + beta p;  q = A p, p.q -> alpha;  r -= alpha q, r.r (and r.z_old)
   linear<false>(h, g.len, LinPUpd<TV>{z, h->cp, h->cx, h->dsc, 0.0, 0.0}, MG_K_CG_DIR);
   int nb = zmarch<true>(h, g, OpApplyPQ{h->cp, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64}, MG_K_CG_APPLY, 0);
@@ -1505,6 +1519,7 @@ mg_status cg_iteration(mg_handle* h, TV* z, const Geom& g, const LevelBuf& L0) {
 constexpr double QUEUE_MARGIN = 8.0;  // on the squared residual norm
 
 template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  NvtxRange range("mg CG solve");
   using TV = typename I::TVt;
   auto t0 = clk::now();
   const Geom& g = h->lv[0].g;
@@ -1959,6 +1974,7 @@ template <class I, bool FLEX> mg_status slab_record(mg_handle* h) {
 // The decomposed CG solve: the steps of solve_impl with every vector split
 // over the slabs.
 template <class I> mg_status slab_solve(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  NvtxRange range("mg z-slab CG solve");
   auto t0 = clk::now();
   const mg_params& p = h->prm;
   const int S = (int)h->slab.size();  // the slabs this process holds
@@ -2099,6 +2115,7 @@ void mdot(mg_handle* h, const double* w, const double* V0, int nv, double* dst) 
 }
 
 template <class I> mg_status fgmres_impl(mg_handle* h, const double* f, double* x, double rtol, mg_stats* st) {
+  NvtxRange range("mg FGMRES solve");
   using TV = typename I::TVt;
   auto t0 = clk::now();
   const Geom& g = h->lv[0].g;
@@ -2298,6 +2315,7 @@ mg_status mg_params_default(mg_params* p) {
 
 mg_status mg_setup(mg_handle** out, int Nx, int Ny, int Nz, const double* k_cells, int k_on_device,
                    const mg_params* prm, void* stream) {
+  NvtxRange range("mg setup");
   auto t0 = clk::now();
   if (!out || !k_cells) return fail(nullptr, MG_ERR_ARG, "null handle or k pointer");
   *out = nullptr;
