@@ -535,7 +535,7 @@ void finish(mg_handle* h, int nblocks, int mode, Scal* mirror = nullptr) {
     return;
   }
   int flex = h->prm.flexible;
-  launch(h, k_finish, dim3(1), dim3(256), 0, (const double*)h->partials, nblocks, h->pstride, mode, h->dsc, flex,
+  launch(h, k_finish, dim3(1), dim3(FIN_THREADS), 0, (const double*)h->partials, nblocks, h->pstride, mode, h->dsc, flex,
          mirror);
   ++h->launches;
 }
@@ -1847,7 +1847,7 @@ mg_status slab_exchange(mg_handle* h, const std::vector<std::vector<Pass>>& R, s
 mg_status slab_finish(mg_handle* h, const int* nbs, int mode) {
   const int S = h->nslab;
   if (h->rank_mode) {  // this rank's sums, summed over the ranks by the transport
-    launch(h, k_finish_partial, dim3(1), dim3(256), 0, (const double*)h->slab[0]->partials, nbs[0],
+    launch(h, k_finish_partial, dim3(1), dim3(FIN_THREADS), 0, (const double*)h->slab[0]->partials, nbs[0],
            h->slab[0]->pstride, h->tr.reduce_buf, 1);
     CKL();
     if (h->tr.allreduce(h->tr.ctx, 2, (void*)h->s) != 0) return fail(h, MG_ERR_CUDA, "slab transport: all-reduce failed");
@@ -1856,7 +1856,7 @@ mg_status slab_finish(mg_handle* h, const int* nbs, int mode) {
     return MG_OK;
   }
   for (int s = 0; s < S; ++s)
-    launch(h, k_finish_partial, dim3(1), dim3(256), 0, (const double*)h->slab[s]->partials, nbs[s],
+    launch(h, k_finish_partial, dim3(1), dim3(FIN_THREADS), 0, (const double*)h->slab[s]->partials, nbs[s],
            h->slab[s]->pstride, h->slots + s, S);
   launch(h, k_combine, dim3(1), dim3(32), 0, (const double*)h->slots, S, mode, h->dsc, h->prm.flexible);
   h->launches += S + 1;

@@ -399,20 +399,46 @@ __device__ __forceinline__ void finish_apply(double a0, double a1, int mode, Sca
   }
 }
 
-// Sums partials[0..n) (and partials[stride..stride+n)) in a fixed order and
-// updates the CG scalars.  One block of 256 threads.  With mirror (host
-// memory mapped into the device's address space) the updated scalars are
-// also written there, so that the host can read them after this kernel
-// without a copy queued on the stream.
-__global__ void __launch_bounds__(256) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
-                                                int flexible, Scal* mirror) {
-  pdl_wait();
-  double a0 = 0.0, a1 = 0.0;
-  for (int t = threadIdx.x; t < n; t += 256) {
-    a0 += partials[t];
-    a1 += partials[stride + t];
+// Fixed-order sum of partials[0..n) (and, with two, of partials[stride ..
+// stride+n)) by one block of FIN_THREADS threads: thread t adds elements
+// t, t + FIN_THREADS, ... into four accumulators in turn, so that four
+// independent loads are in flight per thread, then adds the four in a fixed
+// order; the block sum follows.  Only the flexible CG's residual update needs
+// the second sum.
+constexpr int FIN_THREADS = 256;
+__device__ __forceinline__ void fin_sum(const double* part, int n, int stride, bool two, double& a0, double& a1) {
+  double s0[4] = {0.0, 0.0, 0.0, 0.0}, s1[4] = {0.0, 0.0, 0.0, 0.0};
+  int t = threadIdx.x;
+  for (; t + 3 * FIN_THREADS < n; t += 4 * FIN_THREADS) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s0[u] += part[t + u * FIN_THREADS];
+    if (two) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s1[u] += part[stride + t + u * FIN_THREADS];
+    }
   }
-  block_sum2<256>(a0, a1);
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {  // at most three elements are left
+    const int q = t + u * FIN_THREADS;
+    if (q < n) {
+      s0[u] += part[q];
+      if (two) s1[u] += part[stride + q];
+    }
+  }
+  a0 = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+  a1 = (s1[0] + s1[1]) + (s1[2] + s1[3]);
+  block_sum2<FIN_THREADS>(a0, a1);
+}
+
+// Sums the per-block partials of a reduction and updates the CG scalars.
+// With mirror (host memory mapped into the device's address space) the
+// updated scalars are also written there, so that the host can read them
+// after this kernel without a copy queued on the stream.
+__global__ void __launch_bounds__(FIN_THREADS) k_finish(const double* partials, int n, int stride, int mode, Scal* s,
+                                                        int flexible, Scal* mirror) {
+  pdl_wait();
+  double a0, a1;
+  fin_sum(partials, n, stride, mode == FIN_RR && flexible, a0, a1);
   if (threadIdx.x == 0) {
     finish_apply(a0, a1, mode, s, flexible);
     if (mirror) {
@@ -424,15 +450,11 @@ __global__ void __launch_bounds__(256) k_finish(const double* partials, int n, i
 
 // z-slab decomposition: one slab's reduction summed as k_finish sums it, into
 // slot[0] and slot[nslab] instead of the scalars ...
-__global__ void __launch_bounds__(256) k_finish_partial(const double* partials, int n, int stride, double* slot,
-                                                        int nslab) {
+__global__ void __launch_bounds__(FIN_THREADS) k_finish_partial(const double* partials, int n, int stride, double* slot,
+                                                                int nslab) {
   pdl_wait();
-  double a0 = 0.0, a1 = 0.0;
-  for (int t = threadIdx.x; t < n; t += 256) {
-    a0 += partials[t];
-    a1 += partials[stride + t];
-  }
-  block_sum2<256>(a0, a1);
+  double a0, a1;
+  fin_sum(partials, n, stride, true, a0, a1);
   if (threadIdx.x == 0) {
     slot[0] = a0;
     slot[nslab] = a1;
