@@ -443,6 +443,11 @@ MG_HALO_OF(class R MG_COMMA class TV MG_COMMA class TB MG_COMMA class TC,
            OpResidual27<R MG_COMMA TV MG_COMMA TB MG_COMMA TC>, op.x, TV, g)
 #undef MG_HALO_OF
 #undef MG_COMMA
+template <class TB> struct HaloOf<OpResidualD<TB>> {
+  static void* ptr(const OpResidualD<TB>& op) { return (void*)op.x; }
+  static int bytes() { return 8; }
+  static Geom geom(const OpResidualD<TB>&, const Geom& g) { return g; }
+};
 template <> struct HaloOf<OpApplyPQ> {
   static void* ptr(const OpApplyPQ& op) { return (void*)op.p; }
   static int bytes() { return 8; }
@@ -854,6 +859,11 @@ template <class TV, class TC> struct Impl {
                                          MG_K_RESID);
     } else if (Lv.g27) {
       OpResidual27<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.w), Lv.g.len, V(Lv.dg)};
+      zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
+    } else if (std::is_same<TV, double>::value && l == 0 && !h->rec && !h->sub) {
+      // float64 form, finest level: the stored float64 diagonal
+      OpResidualD<double> res{(const double*)Lv.x[cur], (const double*)Lv.b, (double*)Lv.r, h->dg64,
+                              (const double*)Lv.kx, (const double*)Lv.ky, (const double*)Lv.kz};
       zmarch<false>(h, Lv.g, res, MG_K_RESID, l);
     } else {
       OpResidual<TV, TV, TV, TC> res{V(Lv.x[cur]), V(Lv.b), V(Lv.r), C(Lv.kx), C(Lv.ky), C(Lv.kz)};
@@ -1536,7 +1546,7 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
   finish(h, nb, FIN_BB);
   if (p.nonzero_guess) {
     if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
-    OpResidual<double, double, double, double> res{h->cx, h->cb, h->cr, L0.kx64, L0.ky64, L0.kz64};
+    OpResidualD<double> res{h->cx, h->cb, h->cr, h->dg64, L0.kx64, L0.ky64, L0.kz64};
     nb = zmarch<true>(h, g, res);
     finish(h, nb, FIN_RR);
   } else {
@@ -1627,7 +1637,7 @@ template <class I> mg_status solve_impl(mg_handle* h, const double* f, double* x
   }
   if ((s = unpack_level(h, 0, h->cx, x, true)) != MG_OK) return s;
   // true residual in float64
-  OpResidual<double, double, double, double> res{h->cx, h->cb, h->cq, L0.kx64, L0.ky64, L0.kz64};
+  OpResidualD<double> res{h->cx, h->cb, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64};
   nb = zmarch<true>(h, g, res);
   finish(h, nb, FIN_TRUE);
   if ((s = read_scal(h)) != MG_OK) return s;
@@ -2088,13 +2098,18 @@ mg_status fgmres_alloc(mg_handle* h) {
   if (h->kv) return MG_OK;
   const i64 n = h->lv[0].g.len;
   const int m = h->prm.gmres_restart;
-  h->kgrid = h->nsm * 4;
+  int per_sm = 0;  // one wave of the multi-dot kernel's resident blocks
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdot, KR_THREADS, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 2;
+  }
+  h->kgrid = h->nsm * per_sm;
   AL(h->kv, double, (i64)(m + 1) * n);
   void* q;
   AL(q, char, (i64)m * n * (i64)vbytes(h));
   h->kz = q;
   AL(h->kh, double, 2 * (i64)(m + 2));
-  AL(h->kpart, double, (i64)KR_MAXV * h->kgrid);
+  AL(h->kpart, double, std::max((i64)KR_MAXV * h->kgrid, (i64)lin_blocks(h, n)));  // k_mdot's and k_maxpy's partials
   if (cudaMallocHost(&h->khost, sizeof(double) * 2 * (m + 2)) != cudaSuccess) {
     cudaGetLastError();
     h->khost = nullptr;
@@ -2150,7 +2165,7 @@ template <class I> mg_status fgmres_impl(mg_handle* h, const double* f, double* 
   bool converged = false;
   while (bnorm > 0.0) {
     // restart from the true residual r = b - A x
-    OpResidual<double, double, double, double> res{h->cx, h->cb, h->cr, L0.kx64, L0.ky64, L0.kz64};
+    OpResidualD<double> res{h->cx, h->cb, h->cr, h->dg64, L0.kx64, L0.ky64, L0.kz64};
     nb = zmarch<true>(h, g, res);
     finish(h, nb, FIN_RR);
     if ((s = read_scal(h)) != MG_OK) return s;
@@ -2187,11 +2202,12 @@ template <class I> mg_status fgmres_impl(mg_handle* h, const double* f, double* 
       if ((s = run_precondition<I>(h, &zp)) != MG_OK) return s;
       CK(cudaMemcpyAsync(Zj, zp, (size_t)n * sizeof(TV), cudaMemcpyDeviceToDevice, h->s));
       // w = A z_j, then classical Gram-Schmidt against v_0..v_j
-      zmarch<false>(h, g, OpApplyTo64<TV>{Zj, h->cw, L0.kx64, L0.ky64, L0.kz64});
+      zmarch<false>(h, g, OpApplyTo64<TV>{Zj, h->cw, h->dg64, L0.kx64, L0.ky64, L0.kz64});
       mdot(h, h->cw, V, j + 1, h->kh);
-      k_maxpy<double, true><<<lb, 256, 0, h->s>>>(h->cw, V, n, j + 1, h->kh, n);
-      ++h->launches;
-      mdot(h, h->cw, h->cw, 1, h->kh + j + 1);
+      // w -= V h, with the block sums of w.w of the updated w
+      k_maxpy<double, true, true><<<lb, KR_THREADS, 0, h->s>>>(h->cw, V, n, j + 1, h->kh, n, h->kpart);
+      k_mdot_finish<<<1, KR_THREADS, 0, h->s>>>(h->kpart, lb, h->kh + j + 1);
+      h->launches += 2;
       CK(cudaMemcpyAsync(h->khost, h->kh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, h->s));
       CK(cudaStreamSynchronize(h->s));
       tm_collect(h);
@@ -2243,7 +2259,7 @@ template <class I> mg_status fgmres_impl(mg_handle* h, const double* f, double* 
     if (jj > 0) {
       for (int i = 0; i < jj; ++i) h->khost[i] = y[i];
       CK(cudaMemcpyAsync(h->kh, h->khost, sizeof(double) * jj, cudaMemcpyHostToDevice, h->s));
-      k_maxpy<TV, false><<<lb, 256, 0, h->s>>>(h->cx, Z, n, jj, h->kh, n);
+      k_maxpy<TV, false, false><<<lb, KR_THREADS, 0, h->s>>>(h->cx, Z, n, jj, h->kh, n, nullptr);
       ++h->launches;
       CK(cudaStreamSynchronize(h->s));  // the pinned y is reused by the next cycle
     }
@@ -2257,7 +2273,7 @@ template <class I> mg_status fgmres_impl(mg_handle* h, const double* f, double* 
   if (result == MG_OK && bnorm > 0.0 && !converged)
     result = fail(h, MG_ERR_NOT_CONVERGED, "maximum number of iterations reached");
   if ((s = unpack_level(h, 0, h->cx, x, true)) != MG_OK) return s;
-  OpResidual<double, double, double, double> res{h->cx, h->cb, h->cq, L0.kx64, L0.ky64, L0.kz64};
+  OpResidualD<double> res{h->cx, h->cb, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64};
   nb = zmarch<true>(h, g, res);
   finish(h, nb, FIN_TRUE);
   if ((s = read_scal(h)) != MG_OK) return s;
@@ -2630,7 +2646,7 @@ mg_status mg_residual_norm(mg_handle* h, const double* f, const double* x, doubl
   mg_status s;
   if ((s = pack_level(h, 0, f, h->cb, true)) != MG_OK) return s;
   if ((s = pack_level(h, 0, x, h->cx, true)) != MG_OK) return s;
-  OpResidual<double, double, double, double> res{h->cx, h->cb, h->cq, L0.kx64, L0.ky64, L0.kz64};
+  OpResidualD<double> res{h->cx, h->cb, h->cq, h->dg64, L0.kx64, L0.ky64, L0.kz64};
   const int nb = zmarch<true>(h, L0.g, res);
   finish(h, nb, FIN_TRUE);
   if ((s = read_scal(h)) != MG_OK) return s;

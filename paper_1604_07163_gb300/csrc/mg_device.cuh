@@ -307,6 +307,29 @@ template <class R, class TV, class TB, class TC> struct OpResidual {
   }
 };
 
+// r = b - A x in float64 with the stored diagonal dg (the finest level's sum
+// of the six edge coefficients, in stencil()'s order, so the value is that of
+// OpResidual bit for bit).  On GB300's float64 pipe, forming D again would cost
+// five additions per point in a kernel that the pipe bounds.
+template <class TB> struct OpResidualD {
+  using Real = double;
+  const double* x;
+  const TB* b;
+  double* r;
+  const double* dg;
+  const double *kx, *ky, *kz;
+  __device__ void prepare() {}
+  template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double& acc,
+                                                        double&) const {
+    double D;
+    LdVec<NC, double, double> lx{x};
+    const double S = stencil<NC, double>(g, p, lx, kx, ky, kz, D);
+    const double rv = (cvt<double>(ldp<NC>(b + p)) + S) - ldp<NC>(dg + p) * lx(p);
+    r[p] = rv;
+    acc = fma(rv, rv, acc);
+  }
+};
+
 // Full weighting bc = R r, R = P^T / 8: weights (1/4, 1/2, 1/4) per axis
 // around fine point (2i+1, 2j+1, 2k+1), the image of coarse point (i,j,k).
 // Runs over the coarse grid; gf is the fine geometry.

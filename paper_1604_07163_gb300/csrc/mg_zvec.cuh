@@ -306,6 +306,47 @@ template <class R_, class TV, class TB, class TC_> struct Zv<OpResidual<R_, TV, 
   }
 };
 
+// float64 r = b - A x with the stored diagonal
+template <class TB> struct Zv<OpResidualD<TB>> {
+  using Op = OpResidualD<TB>;
+  using R = double;
+  using TC = double;
+  using UU = ZvVecU<double, double>;
+  using U = typename UU::U;
+  struct P {
+    double b[2], dg[2];
+  };
+  static constexpr bool ok = true;
+  static __device__ __forceinline__ const TC* kx(const Op& o) { return o.kx; }
+  static __device__ __forceinline__ const TC* ky(const Op& o) { return o.ky; }
+  static __device__ __forceinline__ const TC* kz(const Op& o) { return o.kz; }
+  static __device__ __forceinline__ void load_u(const Op& o, int p, U& u) { UU::load(o.x, p, u); }
+  static __device__ __forceinline__ void vals(const Op&, const U& u, double (&v)[2]) { UU::vals(u, v); }
+  static __device__ __forceinline__ double u_one(const Op& o, int q) { return UU::one(o.x, q); }
+  static __device__ __forceinline__ void load_p(const Op& o, int p, P& q) {
+    ld2(o.b + p, q.b);
+    ld2(o.dg + p, q.dg);
+  }
+  static __device__ __forceinline__ void prefetch(const Op& o, int qp, int qu) {
+    pf_l2(o.x + qu);
+    pf_l2(o.b + qp);
+    pf_l2(o.dg + qp);
+  }
+  static __device__ __forceinline__ void emit(const Op& o, int p, int nv, const ZvNb<double>& nb, const U&, const P& q,
+                                              double& acc, double&) {
+    double rv[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      double D;
+      const double S = nb.eval(e, D);
+      rv[e] = (q.b[e] + S) - q.dg[e] * nb.uc[e];
+    }
+    st2(o.r + p, rv, nv);
+    if (nv > 0) acc = fma(rv[0], rv[0], acc);
+    if (nv > 1) acc = fma(rv[1], rv[1], acc);
+  }
+};
+
 // (The float64 CG operator, OpApplyPQ, stays on the scalar driver: it is bound
 // by the float64 pipe, and the scalar kernel measured 3% faster on it.)
 
