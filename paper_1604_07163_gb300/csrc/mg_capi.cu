@@ -2099,7 +2099,8 @@ mg_status fgmres_alloc(mg_handle* h) {
   const i64 n = h->lv[0].g.len;
   const int m = h->prm.gmres_restart;
   int per_sm = 0;  // one wave of the multi-dot kernel's resident blocks
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdot, KR_THREADS, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdot<KR_MAXV>, KR_THREADS, 0) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     per_sm = 2;
   }
@@ -2123,9 +2124,22 @@ void mdot(mg_handle* h, const double* w, const double* V0, int nv, double* dst) 
   const i64 n = h->lv[0].g.len;
   for (int c = 0; c < nv; c += KR_MAXV) {
     const int k = nv - c < KR_MAXV ? nv - c : KR_MAXV;
-    k_mdot<<<h->kgrid, KR_THREADS, 0, h->s>>>(w, V0 + (i64)c * n, n, k, n, h->kpart);
-    k_mdot_finish<<<k, KR_THREADS, 0, h->s>>>(h->kpart, h->kgrid, dst + c);
-    h->launches += 2;
+    const double* Vc = V0 + (i64)c * n;
+    // chunks of 8, 4, 2 or 1 vectors (the kernel keeps 8 vectors' worth of loads in flight).
+    // Grids measured on GB300 at 255^3: 2 blocks per SM for 8 and 4 vectors, 3 for 2 and 1.
+    for (int d = 0; d < k;) {
+      const int r = k - d, q = r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
+      const int grid = std::min(h->kgrid, h->nsm * (q >= 4 ? 2 : 3));
+      switch (q) {
+        case 8: k_mdot<8><<<grid, KR_THREADS, 0, h->s>>>(w, Vc + (i64)d * n, n, n, h->kpart); break;
+        case 4: k_mdot<4><<<grid, KR_THREADS, 0, h->s>>>(w, Vc + (i64)d * n, n, n, h->kpart); break;
+        case 2: k_mdot<2><<<grid, KR_THREADS, 0, h->s>>>(w, Vc + (i64)d * n, n, n, h->kpart); break;
+        default: k_mdot<1><<<grid, KR_THREADS, 0, h->s>>>(w, Vc + (i64)d * n, n, n, h->kpart); break;
+      }
+      k_mdot_finish<<<q, KR_THREADS, 0, h->s>>>(h->kpart, grid, dst + c + d);
+      h->launches += 2;
+      d += q;
+    }
   }
 }
 

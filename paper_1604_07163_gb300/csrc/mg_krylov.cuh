@@ -14,25 +14,51 @@ constexpr int KR_MAXV = 8;    // vectors per multi-dot launch
 constexpr int KR_MAXC = 264;  // coefficients of one k_maxpy launch (at most the restart length + 1)
 
 // partials[v * nblocks + block] = sum over this block's elements of w . V_v,
-// for the nv <= KR_MAXV vectors V_v = V0 + v * vst.
+// for the NV <= KR_MAXV vectors V_v = V0 + v * vst.  The pass is bound by
+// load latency unless each thread keeps enough loads in flight: a thread
+// takes 2U consecutive elements per step (U = 8 / NV pairs), issues all of the
+// step's 16-byte loads of w and of every V_v, then its multiply-adds.
+template <int NV>
 __global__ void __launch_bounds__(KR_THREADS) k_mdot(const double* __restrict__ w, const double* __restrict__ V0,
-                                                     i64 vst, int nv, i64 n, double* partials) {
-  double acc[KR_MAXV];
+                                                     i64 vst, i64 n, double* partials) {
+  constexpr int U = KR_MAXV / NV;  // element pairs per thread and step
+  double acc[NV];
 #pragma unroll
-  for (int v = 0; v < KR_MAXV; ++v) acc[v] = 0.0;
-  for (i64 t = blockIdx.x * (i64)KR_THREADS + threadIdx.x; t < n; t += (i64)gridDim.x * KR_THREADS) {
-    const double wt = w[t];
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  const i64 step = 2 * U * (i64)gridDim.x * KR_THREADS;
+  i64 t0 = 2 * U * (blockIdx.x * (i64)KR_THREADS) + 2 * threadIdx.x;
+  for (; t0 + 2 * (U - 1) * KR_THREADS < n; t0 += step) {  // all U pairs in range
+    double2 wt[U], x[U][NV];
 #pragma unroll
-    for (int v = 0; v < KR_MAXV; ++v)
-      if (v < nv) acc[v] = fma(wt, V0[v * vst + t], acc[v]);
+    for (int u = 0; u < U; ++u) {
+      const i64 t = t0 + 2 * u * KR_THREADS;
+      wt[u] = __ldg(reinterpret_cast<const double2*>(w + t));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) x[u][v] = __ldg(reinterpret_cast<const double2*>(V0 + v * vst + t));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = fma(wt[u].y, x[u][v].y, fma(wt[u].x, x[u][v].x, acc[v]));
+  }
+  for (int u = 0; u < U; ++u) {  // the last, partial step
+    const i64 t = t0 + 2 * u * KR_THREADS;
+    if (t < n) {
+      const double2 wt = __ldg(reinterpret_cast<const double2*>(w + t));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double2 x = __ldg(reinterpret_cast<const double2*>(V0 + v * vst + t));
+        acc[v] = fma(wt.y, x.y, fma(wt.x, x.x, acc[v]));
+      }
+    }
   }
 #pragma unroll
-  for (int v = 0; v < KR_MAXV; v += 2) {
-    double a = acc[v], b = acc[v + 1];
+  for (int v = 0; v < NV; v += 2) {
+    double a = acc[v], b = v + 1 < NV ? acc[v + 1] : 0.0;
     block_sum2<KR_THREADS>(a, b);
     if (threadIdx.x == 0) {
-      if (v < nv) partials[(i64)v * gridDim.x + blockIdx.x] = a;
-      if (v + 1 < nv) partials[(i64)(v + 1) * gridDim.x + blockIdx.x] = b;
+      partials[(i64)v * gridDim.x + blockIdx.x] = a;
+      if (v + 1 < NV) partials[(i64)(v + 1) * gridDim.x + blockIdx.x] = b;
     }
   }
 }
