@@ -316,15 +316,6 @@ def run_ours(args):
     launches = 0
     run_forms = [HEADLINE] + [fm for fm in args.forms.split(",") if fm in FORMS and fm != HEADLINE]
 
-    phi_obs = None
-    if args.adjoint:  # loss 0.5 |phi - phi_obs|^2 with phi_obs from the k field of seed + 1
-        kobs = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed + 1), device=dev)
-        So = new_solver(kobs, precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit,
-                        coarse_op=args.coarse_op)
-        phi_obs, _ = So.solve(f, rtol, raise_on_error=False)
-        So.close()
-        del So
-
     def new_solver(kk, **kw):
         """A solver of the run's parallel layout: in the decomposed run this
         rank's slab of the z-slab decomposition, connected to the others."""
@@ -334,6 +325,15 @@ def run_ours(args):
         if decomposed:
             S.attach_transport()
         return S
+
+    phi_obs = None
+    if args.adjoint:  # loss 0.5 |phi - phi_obs|^2 with phi_obs from the k field of seed + 1
+        kobs = torch.tensor(mi.cell_k(dims, spec["block"], spec["lo"], spec["hi"], seed + 1), device=dev)
+        So = new_solver(kobs, precision=HEADLINE, face_rule=args.face_rule, maxit=args.maxit,
+                        coarse_op=args.coarse_op)
+        phi_obs, _ = So.solve(f, rtol, raise_on_error=False)
+        So.close()
+        del So
 
     def dofs_per_s(ms):
         return n / (ms * 1e-3) if decomposed else whole_job_dofs_per_s(n, world, ms)
