@@ -130,9 +130,10 @@ typedef struct {
                           1 needs a coarsest level of at most 32 unknowns */
   double coarse_rtol;  /* relative residual of the inexact coarse solve (default 1e-4) */
   int coarse_maxit;    /* its iteration limit, 1..32 (default 30) */
-  int bottom_blocks;   /* blocks of the bottom kernel: 0 (default) chosen from the size of its finest
-                          level; 1 one block; 2, 4 or 8 one thread-block cluster that splits every pass.
-                          The result is bitwise the same for every choice */
+  int bottom_blocks;   /* blocks of the bottom kernel: 0 (default) one block, or, in the float64 form and
+                          for Galerkin (27-point) bottom levels, one block per 1024 points of its finest
+                          level up to a cluster of 8; 1 one block; 2, 4 or 8 one thread-block cluster that
+                          splits every pass.  The result is bitwise the same for every choice */
   int test_inject;     /* TEST ONLY: a data perturbation made by the host at setup so that the error paths
                           can be exercised without any GPU fault.  0 (default) none; 1 the float64 finest
                           diagonal used by the outer Krylov operator is negated, so p.Ap < 0 and mg_solve
