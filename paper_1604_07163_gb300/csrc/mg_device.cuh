@@ -363,6 +363,12 @@ template <class R, class TV> struct OpRestrict {
 // each axis a fine index i draws on coarse indices (i-1)>>1 and i>>1 with
 // weight 1/2 each: for odd i both are the coincident coarse point (weight 1),
 // for even i they are its two neighbours; index -1 and n_c are zero pads.
+// The eight terms are summed per coarse column first (the two rows and two
+// planes of column i0, then of column i1), so that the vector kernel, which
+// updates several fine points of a row, forms each column's sum once and
+// shares it: x += (Y(i0) + Y(i1)) / 8 with Y(c) = (e(c,j0,k0) + e(c,j0,k1)) +
+// (e(c,j1,k0) + e(c,j1,k1)).  (Half the floating-point additions of a sum
+// taken point by point, which matters in float64 on GB300.)
 template <class R, class TV> struct OpProlong {
   using Real = R;
   Geom gc;
@@ -375,10 +381,11 @@ template <class R, class TV> struct OpProlong {
     const int a00 = (int)gc.at(i0, j0, k0), a10 = (int)gc.at(i0, j1, k0), a01 = (int)gc.at(i0, j0, k1),
               a11 = (int)gc.at(i0, j1, k1);
     const int di = i1 - i0;
-    R s = cvt<R>(ldp<NC>(e + a00)) + cvt<R>(ldp<NC>(e + a00 + di));
-    s += cvt<R>(ldp<NC>(e + a10)) + cvt<R>(ldp<NC>(e + a10 + di));
-    s += cvt<R>(ldp<NC>(e + a01)) + cvt<R>(ldp<NC>(e + a01 + di));
-    s += cvt<R>(ldp<NC>(e + a11)) + cvt<R>(ldp<NC>(e + a11 + di));
+    auto col = [&](int o) {
+      return (cvt<R>(ldp<NC>(e + a00 + o)) + cvt<R>(ldp<NC>(e + a01 + o))) +
+             (cvt<R>(ldp<NC>(e + a10 + o)) + cvt<R>(ldp<NC>(e + a11 + o)));
+    };
+    const R s = col(0) + col(di);
     x[p] = store_as<TV>(fma((R)0.125, s, cvt<R>(x[p])));
   }
 };

@@ -460,7 +460,8 @@ __global__ void __launch_bounds__(ZV_THREADS, ZvMinBlocks<Op>::value)
 // float32, two in float64); the twelve coarse values they draw on (coarse
 // columns 2m-1 .. 2m+1, two rows, two planes) come through L1.  A thread
 // owns one row chunk, so many independent read-modify-writes are in flight.
-// Same terms in the same order as OpProlong.
+// Same terms in the same order as OpProlong; each coarse column's sum is
+// formed once for the four points.
 constexpr int PV_THREADS = 256;  // 64 chunks of 4 points x 4 rows
 template <class R, class TV>
 __global__ void __launch_bounds__(PV_THREADS) k_prolong_v(OpProlong<R, TV> op, Geom g) {
@@ -492,15 +493,14 @@ __global__ void __launch_bounds__(PV_THREADS) k_prolong_v(OpProlong<R, TV> op, G
       const double2 t1 = *reinterpret_cast<const double2*>(op.x + p + 2);
       xv[0] = t0.x, xv[1] = t0.y, xv[2] = t1.x, xv[3] = t1.y;
     }
+    R Y[3];  // per coarse column: the two rows and two planes, in OpProlong's order
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) Y[cc] = (E[0][0][cc] + E[1][0][cc]) + (E[0][1][cc] + E[1][1][cc]);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       // coarse columns of fine 4m+e: i0 = (4m+e-1)>>1, i1 = (4m+e)>>1, as offsets from 2m-1
       const int c0 = (e + 1) >> 1, c1 = (e + 2) >> 1;
-      R sum = E[0][0][c0] + E[0][0][c1];
-      sum += E[0][1][c0] + E[0][1][c1];
-      sum += E[1][0][c0] + E[1][0][c1];
-      sum += E[1][1][c0] + E[1][1][c1];
-      xv[e] = fma((R)0.125, sum, xv[e]);
+      xv[e] = fma((R)0.125, Y[c0] + Y[c1], xv[e]);
     }
     const int nv = min(g.nx - i, 4);
     if (nv == 4) {
