@@ -594,15 +594,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 450.1 MB; step 1 with r.z: 601.7 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (525.9e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.3e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.4e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.1e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.8e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.6e6, "ddaa00b13b33550a"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.6e6, "ddaa00b13b33550a"),
+    # 450.0 MB; step 1 with r.z: 601.6 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (525.8e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.4e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.4e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.0e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.7e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.7e6, "f0d73be33d0a751e"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.5e6, "f0d73be33d0a751e"),
 }
 
 
