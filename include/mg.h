@@ -363,6 +363,20 @@ mg_status mg_timing_enable(mg_handle* h, int class_mask, int level_mask);
  * launches and interior points processed (summed over launches). */
 mg_status mg_timing_read(const mg_handle* h, int cls, int l, double* ms, long long* launches, double* points);
 
+/* ---- float64 FMA throughput (measurement helper; not part of the method) --
+ * The outer Krylov operator q = A p in float64 does eight float64 FMAs per
+ * finest point against one neighbour load each, so on GPUs with a narrow
+ * float64 pipe its bound is the float64 FMA rate, not memory bandwidth.  This
+ * call measures that rate on the current device: a kernel of independent FMA
+ * chains (8 per thread, 4 blocks of 256 threads per SM, about 16 ms per launch
+ * on a GPU with two float64 FMAs per clock per SM) on a stream of its own, one
+ * untimed launch and then `launches` (1..100) launches timed with CUDA events.
+ * Writes the fastest launch's rate to *tflops in TFLOP/s (one FMA = 2 flops).
+ * Allocates and frees a small device buffer; synchronises its own stream.
+ * Returns MG_ERR_ARG for launches outside 1..100 or a null tflops, MG_ERR_CUDA
+ * if a CUDA call fails. */
+mg_status mg_fp64_fma_peak(int launches, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ EXPORTS = [
     "mg_num_levels", "mg_level_dims", "mg_level_interval", "mg_history", "mg_apply", "mg_smooth", "mg_residual_restrict",
     "mg_prolong_add", "mg_coarse_solve", "mg_vcycle", "mg_gradient", "mg_residual_norm", "mg_timing_enable",
     "mg_timing_read", "mg_residual_norm_noalloc", "mg_solve_host", "mg_slab_plan", "mg_slab_transport_sizes",
-    "mg_set_transport",
+    "mg_set_transport", "mg_fp64_fma_peak",
 ]
 KERNEL_CLASSES = ["cheb_zero", "cheb_step", "resid", "restrict", "prolong", "bottom", "cg_dir", "cg_upd", "dot",
                   "cast", "cg_apply", "host_gap"]
@@ -110,6 +110,7 @@ def load():
         "mg_timing_enable": ([vp, i, i], i),
         "mg_residual_norm_noalloc": ([vp, vp, vp, vp], i),
         "mg_timing_read": ([vp, i, i, P(C.c_double), P(C.c_longlong), P(C.c_double)], i),
+        "mg_fp64_fma_peak": ([i, P(C.c_double)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

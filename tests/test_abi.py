@@ -108,3 +108,10 @@ def test_source_hash_ignores_comments_only():
     code = {"k.cu": "// a kernel\n__global__ void k(float* x) { x[0] = 2.0f; /* store */ }\n"}
     assert bench.csrc_hash(base) == bench.csrc_hash(comment)
     assert bench.csrc_hash(base) != bench.csrc_hash(code)
+
+
+def test_fp64_rate_probe_rejects_bad_arguments_before_touching_the_device(lib):
+    r = ctypes.c_double()
+    assert lib.mg_fp64_fma_peak(0, ctypes.byref(r)) == 1
+    assert lib.mg_fp64_fma_peak(101, ctypes.byref(r)) == 1
+    assert lib.mg_fp64_fma_peak(3, None) == 1
