@@ -54,14 +54,14 @@ def bytes_per_point(cls: str, v: int, c: int, degree: int = 2, fp64: bool = Fals
     dinv = v if fp64 else 0
     return {
         "cheb_zero": 3 * v + c + (v if degree > 2 else 0),  # read b, dinv, k; write x (and d)
-        "cheb_step": 4 * v + c + 4 + dinv,                # (x+b+k+x'+d) and (x+d+b+k+z+r64), averaged
+        "cheb_step": 4 * v + c + dinv,                    # (x+b+k+x'+d) and (x+d+b+k+z), averaged
         "resid": 3 * v + c,                               # read x, b, k; write r
         "restrict": 9 * v,                                # per coarse point: read 8 fine r, write 1
         "prolong": 2 * v + v / 8,                         # read x, e/8; write x
         "cg_dir": 32 + v,                                 # read z, p, x; write p, x (float64 p, x)
         "cg_apply": 3 * 8 + 24,                           # read p, D, k64; write q (float64)
         "cg_upd": 24 + (0 if fp64 else 4) + (v if flexible else 0),  # read r, q (z); write r (, float32 b)
-        "dot": 8 + v,                                     # read r (float64), z
+        "dot": 2 * v,                                     # read b, z
         "cast": 12,                                       # float64 r -> float32 b
     }[cls]
 
@@ -604,15 +604,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 450.0 MB; step 1 with r.z: 601.6 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (525.8e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.4e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.4e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.0e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.7e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.7e6, "f0d73be33d0a751e"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.5e6, "f0d73be33d0a751e"),
+    # 449.8 MB; step 1 with b.z: 461.0 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (455.4e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.5e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.1e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.1e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.9e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.7e6, "ede762600c9e5c70"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.6e6, "ede762600c9e5c70"),
 }
 
 

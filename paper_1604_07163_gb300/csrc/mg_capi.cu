@@ -40,7 +40,7 @@ struct LevelBuf {
   void *d = nullptr, *b = nullptr, *r = nullptr;
   // TMA tensor maps (2-D row views) for the staged stencil kernels
   bool tma = false;
-  CUtensorMap m_full_x[2], m_full_b, m_full_dinv, m_kx, m_ky, m_kz, m_c_dinv, m_c_b, m_c_d, m_c_r64;
+  CUtensorMap m_full_x[2], m_full_b, m_full_dinv, m_kx, m_ky, m_kz, m_c_dinv, m_c_b, m_c_d;
   int tma_grid[3] = {0, 0, 0}, tma_kchunk = 0;
   // Galerkin (27-point) level: couplings w (13 arrays, V-cycle precision) and
   // their float64 copies, diagonal in the V-cycle precision and in float64
@@ -613,7 +613,6 @@ template <class TV, class TC> struct Impl {
     ok = ok && tma_encode<TV>(&Lv.m_c_dinv, Lv.dinv, g, TT_X, TT_Y);
     ok = ok && tma_encode<TV>(&Lv.m_c_b, Lv.b, g, TT_X, TT_Y);
     ok = ok && tma_encode<TV>(&Lv.m_c_d, Lv.d, g, TT_X, TT_Y);
-    if (l == 0) ok = ok && tma_encode<double>(&Lv.m_c_r64, h->cr, g, TT_X, TT_Y);
     if (!ok) return false;
     // grid: 32x8 tiles; planes split so that about one wave of blocks is
     // resident (shared memory bounds the blocks per SM)
@@ -655,7 +654,6 @@ template <class TV, class TC> struct Impl {
     maps.m[5] = Lv.m_c_dinv;
     maps.m[6] = Lv.m_c_b;
     maps.m[7] = Lv.m_c_d;
-    if (DOT) maps.m[8] = Lv.m_c_r64;
     TmaArgs<TV, TC> a{};
     a.g = Lv.g;
     a.kchunk = Lv.tma_kchunk;
@@ -717,7 +715,7 @@ template <class TV, class TC> struct Impl {
       } else {
         OpChebStep<TV, TV, TC> op{V(Lv.x[cur]), dprev, V(Lv.b), V(Lv.dinv), xo, dout, C(Lv.kx), C(Lv.ky), C(Lv.kz),
                                   (TV)c1, (TV)c2, inv_theta};
-        if (dot) nb = zmarch<true>(h, Lv.g, OpChebStepDot<TV, TV, TC>{op, h->cr}, MG_K_CHEB_STEP, l);
+        if (dot) nb = zmarch<true>(h, Lv.g, OpChebStepDot<TV, TV, TC>{op}, MG_K_CHEB_STEP, l);
         else zmarch<false>(h, Lv.g, op, MG_K_CHEB_STEP, l);
       }
       if (dot) {
@@ -901,16 +899,16 @@ template <class TV, class TC> struct Impl {
     return correct_and_post_smooth(h, l, cur, ccur, fuse_rz);
   }
 
-  // z = M^-1 r; the finest right-hand side (the float64 residual, or its
-  // float32 copy in the mixed forms) must be in place.  Ends with rho = r.z
-  // and the CG beta in the scalar block.  Returns the level-0 buffer (type TV)
-  // holding z.
+  // z = M^-1 r; the finest right-hand side b (the float64 residual, or its
+  // float32 copy in the mixed forms) must be in place.  Ends with rho = b.z
+  // (OpChebStepDot) and the CG beta in the scalar block.  Returns the level-0
+  // buffer (type TV) holding z.
   static TV* precondition(mg_handle* h) {
     LevelBuf& L0 = h->lv[0];
     h->rz_fused = false;
     const int zc = vcycle(h, 0, true);
     if (!h->rz_fused) {
-      const int nb = linear<true>(h, L0.g.len, LinDot<TV>{h->cr, V(L0.x[zc])}, MG_K_DOT);
+      const int nb = linear<true>(h, L0.g.len, LinDotT<TV>{V(L0.b), V(L0.x[zc])}, MG_K_DOT);
       finish(h, nb, FIN_RZ);
     }
     return V(L0.x[zc]);

@@ -544,17 +544,22 @@ template <class TB> struct LinDot {
   }
 };
 
-// Final post-smoothing step on the finest level with the CG dot product
-// rho = r.z fused in: z = x_{j+1} is the V-cycle output, r the float64 residual.
+// Final post-smoothing step on the finest level with the CG dot product rho
+// fused in, accumulated in float64: rho = b.z with z = x_{j+1} the V-cycle's
+// output as stored and b its finest right-hand side as the V-cycle read it.
+// In the float64 form b is the outer residual r itself, so rho = r.z.  In the
+// mixed forms b is the float32 rounding of r, and rho = b^T M b is the
+// quadratic form of the preconditioner M that the float32 V-cycle applies
+// (z = M b); it differs from r.z by at most one float32 rounding of each r
+// entry and saves the pass's float64 read of r.
 template <class R, class TV, class TC> struct OpChebStepDot {
   using Real = R;
   OpChebStep<R, TV, TC> step;
-  const double* r;
   __device__ void prepare() {}
   template <bool NC> __device__ __forceinline__ void pt(const Geom& g, int, int, int, int p, double& a0,
                                                         double&) const {
     const R xn = step.template step<NC>(g, p);
-    a0 = fma(ldp<NC>(r + p), to_double(store_as<TV>(xn)), a0);
+    a0 = fma(to_double(ldp<NC>(step.b + p)), to_double(store_as<TV>(xn)), a0);
   }
 };
 

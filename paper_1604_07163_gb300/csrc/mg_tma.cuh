@@ -41,7 +41,7 @@ constexpr int TMA_POLL_LIMIT = 1 << 20;  // polls of one bounded wait (each may 
 enum TmaKind { TK_STEP = 0, TK_ZERO = 1, TK_RESID = 2 };
 
 struct TmaMaps {
-  CUtensorMap m[9];  // 0 F0, 1 F1, 2 KX, 3 KY, 4 KZ, 5 C0, 6 C1, 7 C2, 8 C3
+  CUtensorMap m[8];  // 0 F0, 1 F1, 2 KX, 3 KY, 4 KZ, 5 C0, 6 C1, 7 C2
 };
 
 // ---- PTX helpers ------------------------------------------------------------
@@ -107,10 +107,8 @@ template <int KIND, bool HAS_D, bool DOT, class TV, class TC> struct TmaLayout {
   static constexpr int C1B = KIND != TK_ZERO ? CB : 0;
   static constexpr int C2 = al128(C1 + C1B);  // STEP with d_{j-1}
   static constexpr int C2B = HAS_D ? CB : 0;
-  static constexpr int C3 = al128(C2 + C2B);  // fused dot: float64 residual
-  static constexpr int C3B = DOT ? TT_X * TT_Y * 8 : 0;
-  static constexpr int STAGE = al128(C3 + C3B);
-  static constexpr int TX_BYTES = F0B + F1B + KXB + KYB + KZB + C0B + C1B + C2B + C3B;
+  static constexpr int STAGE = al128(C2 + C2B);
+  static constexpr int TX_BYTES = F0B + F1B + KXB + KYB + KZB + C0B + C1B + C2B;
   static constexpr int SMEM = TT_NS * STAGE + 128;  // + alignment slack
 };
 
@@ -123,7 +121,7 @@ template <class TV, class TC> struct TmaArgs {
   const TC* kx;      // global kx (for the boundary edge entering each row)
   float c1, c2, inv_theta;
   double dc1, dc2, dinv_theta;
-  double* partials;  // DOT: per-block sums of r.z
+  double* partials;  // DOT: per-block sums of b.z (OpChebStepDot)
   int* status;       // bit ST_TIMEOUT on a wait that gave up
   int poll_limit;    // polls of each wait in the main loop (TMA_POLL_LIMIT; 0 only to test the give-up path)
 };
@@ -171,7 +169,6 @@ __global__ void __launch_bounds__(TT_THREADS) k_tma_stencil(const __grid_constan
     if constexpr (KIND == TK_STEP) tma_load_2d(st + Lay::C0, &maps.m[5], i0, row, &full[s]);
     if constexpr (KIND != TK_ZERO) tma_load_2d(st + Lay::C1, &maps.m[6], i0, row, &full[s]);
     if constexpr (HAS_D) tma_load_2d(st + Lay::C2, &maps.m[7], i0, row, &full[s]);
-    if constexpr (DOT) tma_load_2d(st + Lay::C3, &maps.m[8], i0, row, &full[s]);
   };
   int issued = 0;
   if (tid == 0) {
@@ -248,7 +245,7 @@ __global__ void __launch_bounds__(TT_THREADS) k_tma_stencil(const __grid_constan
         const R xn = u + dn;
         a.xout[p] = store_as<TV>(xn);
         if (a.dout) a.dout[p] = store_as<TV>(dn);
-        if constexpr (DOT) acc = fma(((const double*)(S + Lay::C3))[cc], (double)store_as<TV>(xn), acc);
+        if constexpr (DOT) acc = fma(to_double(((const TV*)(S + Lay::C1))[cc]), to_double(store_as<TV>(xn)), acc);
       }
     }
     __syncthreads();

@@ -187,17 +187,16 @@ template <class R_, class TV, class TC_> struct Zv<OpChebStep<R_, TV, TC_>> {
   }
 };
 
-// last post-smoothing step with rho = r.z accumulated
+// last post-smoothing step with rho = b.z accumulated (OpChebStepDot: b is
+// the right-hand side the step already reads, held exactly in R; both factors
+// are widened on the integer pipe, so the float64 pipe does one FMA per point)
 template <class R_, class TV, class TC_> struct Zv<OpChebStepDot<R_, TV, TC_>> {
   using Op = OpChebStepDot<R_, TV, TC_>;
   using R = R_;
   using TC = TC_;
   using UU = ZvVecU<R, TV>;
   using U = typename UU::U;
-  struct P {
-    ZvStepP<R, TV, TC> s;
-    double r[2];
-  };
+  using P = ZvStepP<R, TV, TC>;
   static constexpr bool ok = true;
   static __device__ __forceinline__ const TC* kx(const Op& o) { return o.step.kx; }
   static __device__ __forceinline__ const TC* ky(const Op& o) { return o.step.ky; }
@@ -205,20 +204,14 @@ template <class R_, class TV, class TC_> struct Zv<OpChebStepDot<R_, TV, TC_>> {
   static __device__ __forceinline__ void load_u(const Op& o, int p, U& u) { UU::load(o.step.x, p, u); }
   static __device__ __forceinline__ void vals(const Op&, const U& u, R (&v)[2]) { UU::vals(u, v); }
   static __device__ __forceinline__ R u_one(const Op& o, int q) { return UU::one(o.step.x, q); }
-  static __device__ __forceinline__ void load_p(const Op& o, int p, P& q) {
-    zv_step_load_p(o.step, p, q.s);
-    ld2(o.r + p, q.r);
-  }
-  static __device__ __forceinline__ void prefetch(const Op& o, int qp, int qu) {
-    zv_step_prefetch(o.step, qp, qu);
-    pf_l2(o.r + qp);
-  }
+  static __device__ __forceinline__ void load_p(const Op& o, int p, P& q) { zv_step_load_p(o.step, p, q); }
+  static __device__ __forceinline__ void prefetch(const Op& o, int qp, int qu) { zv_step_prefetch(o.step, qp, qu); }
   static __device__ __forceinline__ void emit(const Op& o, int p, int nv, const ZvNb<R>& nb, const U&, const P& q,
                                               double& a0, double&) {
     R xn[2];
-    zv_step_emit(o.step, p, nv, nb, q.s, xn);
-    if (nv > 0) a0 = fma(q.r[0], to_double(store_as<TV>(xn[0])), a0);
-    if (nv > 1) a0 = fma(q.r[1], to_double(store_as<TV>(xn[1])), a0);
+    zv_step_emit(o.step, p, nv, nb, q, xn);
+    if (nv > 0) a0 = fma(to_double(store_as<TV>(q.b[0])), to_double(store_as<TV>(xn[0])), a0);
+    if (nv > 1) a0 = fma(to_double(store_as<TV>(q.b[1])), to_double(store_as<TV>(xn[1])), a0);
   }
 };
 
