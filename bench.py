@@ -604,15 +604,15 @@ FP64_FLOP_PER_SM_CLK = 4
 NCU_TRAFFIC = {
     # (workload, form, class): (DRAM bytes per launch, CUDA-source hash at capture)
     # cheb_step: mean of the two finest-level launches per V-cycle (step 0:
-    # 449.8 MB; step 1 with b.z: 461.0 MB)
-    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (455.4e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.5e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.1e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.1e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.9e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.7e6, "ede762600c9e5c70"),
-    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.6e6, "ede762600c9e5c70"),
+    # 450.1 MB; step 1 with b.z: 460.8 MB)
+    ("poisson257_c1e4", "mixed_fp32", "cheb_step"): (455.5e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "cheb_zero"): (396.5e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "resid"): (392.4e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "prolong"): (79.0e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "restrict"): (66.9e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_apply"): (788.8e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_dir"): (547.4e6, "f8447c71119a0be7"),
+    ("poisson257_c1e4", "mixed_fp32", "cg_upd"): (413.4e6, "f8447c71119a0be7"),
 }
 
 

@@ -14,6 +14,8 @@
 // bitwise identical to the one-point-per-thread kernel (only the block sums
 // of the reducing passes group terms differently).
 #pragma once
+#include <type_traits>
+
 #include "mg_device.cuh"
 
 namespace mgdev {
@@ -187,9 +189,35 @@ template <class R_, class TV, class TC_> struct Zv<OpChebStep<R_, TV, TC_>> {
   }
 };
 
+// Compensated dot-product step (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, algorithm Dot2): adds x*y to the
+// float-float accumulator (s, c).  x*y = h + r exactly (TwoProduct via FMA),
+// s + h = t + q exactly (Knuth's TwoSum), and c collects q + r.  After n terms
+// s + c is the dot product with error at most about (n u)^2 sum |x y|, u =
+// 2^-24, i.e. as if summed in twice the float32 precision.  The __f*_rn
+// intrinsics keep the compiler from contracting the product into the sums.
+__device__ __forceinline__ void dot2_add(float x, float y, float& s, float& c) {
+  const float h = __fmul_rn(x, y);
+  const float r = fmaf(x, y, -h);
+  const float t = __fadd_rn(s, h);
+  const float bp = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(q, r));
+}
+
+// Ops whose Zv hooks define float_acc = true sum their per-point terms in a
+// float-float pair per thread (emit_f), which the driver adds into the
+// float64 block sum after its plane loop.
+template <class Z, class = void> struct ZvFloatAcc : std::false_type {};
+template <class Z>
+struct ZvFloatAcc<Z, std::void_t<decltype(Z::float_acc)>> : std::integral_constant<bool, Z::float_acc> {};
+
 // last post-smoothing step with rho = b.z accumulated (OpChebStepDot: b is
-// the right-hand side the step already reads, held exactly in R; both factors
-// are widened on the integer pipe, so the float64 pipe does one FMA per point)
+// the right-hand side the step already reads, held exactly in R).  float64
+// form: one float64 FMA per point.  Float32 V-cycle forms: the products of
+// the float32 b and z are summed per thread with dot2_add on the float32
+// pipe, so the pass needs no widening and no float64 operation per point.
 template <class R_, class TV, class TC_> struct Zv<OpChebStepDot<R_, TV, TC_>> {
   using Op = OpChebStepDot<R_, TV, TC_>;
   using R = R_;
@@ -206,12 +234,20 @@ template <class R_, class TV, class TC_> struct Zv<OpChebStepDot<R_, TV, TC_>> {
   static __device__ __forceinline__ R u_one(const Op& o, int q) { return UU::one(o.step.x, q); }
   static __device__ __forceinline__ void load_p(const Op& o, int p, P& q) { zv_step_load_p(o.step, p, q); }
   static __device__ __forceinline__ void prefetch(const Op& o, int qp, int qu) { zv_step_prefetch(o.step, qp, qu); }
+  static constexpr bool float_acc = sizeof(R) == 4 && sizeof(TV) == 4;
   static __device__ __forceinline__ void emit(const Op& o, int p, int nv, const ZvNb<R>& nb, const U&, const P& q,
                                               double& a0, double&) {
     R xn[2];
     zv_step_emit(o.step, p, nv, nb, q, xn);
     if (nv > 0) a0 = fma(to_double(store_as<TV>(q.b[0])), to_double(store_as<TV>(xn[0])), a0);
     if (nv > 1) a0 = fma(to_double(store_as<TV>(q.b[1])), to_double(store_as<TV>(xn[1])), a0);
+  }
+  static __device__ __forceinline__ void emit_f(const Op& o, int p, int nv, const ZvNb<R>& nb, const U&,
+                                                const P& q, float& s, float& c) {
+    R xn[2];
+    zv_step_emit(o.step, p, nv, nb, q, xn);
+    if (nv > 0) dot2_add((float)q.b[0], (float)store_as<TV>(xn[0]), s, c);
+    if (nv > 1) dot2_add((float)q.b[1], (float)store_as<TV>(xn[1]), s, c);
   }
 };
 
@@ -368,6 +404,7 @@ __global__ void __launch_bounds__(ZV_THREADS, ZvMinBlocks<Op>::value)
   const int k0 = blockIdx.z * kchunk;
   const int k1 = min(k0 + kchunk, g.nz);
   double a0 = 0.0, a1 = 0.0;
+  float f0 = 0.0f, f1 = 0.0f;  // float-float accumulator (ZvFloatAcc ops)
   if (j < g.ny) {
     const int nv = min(max(g.nx - i, 0), 2);
     const int sz = (int)g.sz, sy = g.Px;
@@ -428,7 +465,10 @@ __global__ void __launch_bounds__(ZV_THREADS, ZvMinBlocks<Op>::value)
         nb.cxw = cvt<R>(__ldg(kx + p - 1));
       }
       if (lane == 31) nb.ue = Z::u_one(op, p + 2);
-      if (nv > 0) Z::emit(op, p, nv, nb, qc, pc, a0, a1);
+      if (nv > 0) {
+        if constexpr (ZvFloatAcc<Z>::value) Z::emit_f(op, p, nv, nb, qc, pc, f0, f1);
+        else Z::emit(op, p, nv, nb, qc, pc, a0, a1);
+      }
       qm = qc;
       qc = qp;
       qp = qn;
@@ -438,6 +478,7 @@ __global__ void __launch_bounds__(ZV_THREADS, ZvMinBlocks<Op>::value)
   }
   pdl_trigger();
   if constexpr (RED) {
+    if constexpr (ZvFloatAcc<Z>::value) a0 = (double)f0 + (double)f1;  // exact widening, once per thread
     block_sum2<ZV_THREADS>(a0, a1);
     if (threadIdx.x == 0) {
       const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
