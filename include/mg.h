@@ -64,6 +64,11 @@ typedef enum {
   MG_MIXED_FP32 = 1,  /* V-cycle in float32 (vectors and coefficients) inside float64 CG */
   MG_MIXED_BF16K = 2  /* V-cycle in float32 with bfloat16 edge coefficients inside float64 CG */
 } mg_precision;
+/* In every form CG's rho is b.z, with z the V-cycle's output and b the finest right-hand side it
+ * read: the float64 residual r itself (MG_FP64), or its float32 rounding (mixed forms), which makes
+ * rho = b^T M b for the preconditioner M the float32 V-cycle applies.  It is summed in float64
+ * (in the mixed forms' default kernel each thread first sums its terms as a compensated float32
+ * dot product). */
 
 typedef enum {
   MG_SMOOTHER_CHEBYSHEV = 0,  /* Chebyshev(cheby_degree) preconditioned with Jacobi (Sec. 4.3) */
@@ -350,7 +355,8 @@ typedef enum {
   MG_K_BOTTOM = 5,     /* telescoped bottom levels + coarsest solve, one block or one cluster */
   MG_K_CG_DIR = 6,     /* p = z + beta p (float64) */
   MG_K_CG_UPD = 7,     /* x += alpha p, r -= alpha q, r.r (float64) */
-  MG_K_DOT = 8,        /* r.z (float64 accumulation) */
+  MG_K_DOT = 8,        /* rho = b.z, b the V-cycle's finest right-hand side (float64 accumulation), when
+                          the V-cycle's last step does not form it */
   MG_K_CAST = 9,       /* float64 residual -> float32 V-cycle right-hand side */
   MG_K_CG_APPLY = 10,  /* q = A p, p.q with the float64 outer operator */
   MG_K_HOST_GAP = 11,  /* not a kernel: per outer CG iteration, the device time from the end of the

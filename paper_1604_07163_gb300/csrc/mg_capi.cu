@@ -119,7 +119,7 @@ struct mg_handle {
   std::vector<void*> allocs;
   cudaGraphExec_t vexec = nullptr;
   int vexec_zcur = 0;
-  bool rz_fused = false;         // last V-cycle fused rho = r.z into its final step
+  bool rz_fused = false;         // last V-cycle fused rho = b.z (OpChebStepDot) into its final step
   bool zvec = true;              // stencil passes on the two-points-per-thread driver (k_zvec)
   int lin_grid = 0;              // largest grid of the linear (pointwise) kernels
   long long launches = 0;        // kernels launched (counted at launch sites)
@@ -681,7 +681,7 @@ template <class TV, class TC> struct Impl {
 
   // Chebyshev steps j_from..degree-1 of one sweep on level l: the iterate is in
   // buffer cur (and d_{j_from-1} in Lv.d when j_from > 0), rho_prev = rho_{j_from-1}.
-  // With fuse_rz the last step also accumulates rho = r.z for the outer CG and
+  // With fuse_rz the last step also accumulates rho = b.z for the outer CG and
   // finishes the CG scalars.  Returns the buffer holding the result.
   static int cheb_steps(mg_handle* h, int l, int cur, int j_from, double rho_prev, bool fuse_rz) {
     LevelBuf& Lv = h->lv[l];
@@ -728,7 +728,7 @@ template <class TV, class TC> struct Impl {
   }
 
   // One smoother sweep on level l starting from buffer cur; returns the new cur.
-  // With fuse_rz the last step also accumulates rho = r.z for the outer CG.
+  // With fuse_rz the last step also accumulates rho = b.z for the outer CG.
   static int sweep(mg_handle* h, int l, int cur, bool zero, bool fuse_rz = false) {
     LevelBuf& Lv = h->lv[l];
     const mg_params& p = h->prm;
