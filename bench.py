@@ -394,15 +394,17 @@ def run_ours(args):
             roofline = roofline_from(kt, form, clocks, dom, args.workload)
             smoother = roofline_from(kt, form, clocks, "cheb_step", args.workload)
             if roofline and roofline["bound"] == "alu":
-                # the float64 FMA rate measured on this GPU now, beside the
-                # rate derived from unit counts and the sampled clock
+                # the rate of a float64 FMA-chain kernel on this GPU now, beside
+                # the peak derived from unit counts and the sampled clock: a
+                # lower bound on what the float64 pipe sustains, not its peak
                 fm = fp64_fma_peak()
                 if fm:
-                    roofline["peak_measured"] = fm
-                    roofline["frac_of_measured"] = roofline["achieved"] / fm
-                    roofline["peak_measured_source"] = (
+                    roofline["fp64_probe_tflops"] = fm
+                    roofline["frac_of_probe"] = roofline["achieved"] / fm
+                    roofline["fp64_probe_source"] = (
                         "mg_fp64_fma_peak: independent float64 FMA chains on every SM, fastest of 5 launches "
-                        "of about 16 ms, measured in this run after the timed steps")
+                        "of about 16 ms, in this run after the timed steps; a lower bound on the float64 "
+                        "pipe's rate (the operator itself exceeds it on long launches), not a peak")
             if gt:
                 gap_ms, gap_n, _ = gt
                 host_gap = {"us_per_iteration": 1e3 * gap_ms / gap_n, "ms_per_solve": gap_ms / args.steps,
@@ -658,7 +660,8 @@ def measured_traffic(workload, form, cls):
 
 
 def fp64_fma_peak(launches=5):
-    """Float64 FMA rate of the current GPU in TFLOP/s (library probe), or None."""
+    """Rate of the library's float64 FMA-chain probe on the current GPU in
+    TFLOP/s (a lower bound on the float64 pipe's rate), or None."""
     import ctypes
     from paper_1604_07163_gb300 import _lib
     r = ctypes.c_double()

@@ -373,11 +373,14 @@ mg_status mg_timing_read(const mg_handle* h, int cls, int l, double* ms, long lo
  * The outer Krylov operator q = A p in float64 does eight float64 FMAs per
  * finest point against one neighbour load each, so on GPUs with a narrow
  * float64 pipe its bound is the float64 FMA rate, not memory bandwidth.  This
- * call measures that rate on the current device: a kernel of independent FMA
- * chains (8 per thread, 4 blocks of 256 threads per SM, about 16 ms per launch
- * on a GPU with two float64 FMAs per clock per SM) on a stream of its own, one
- * untimed launch and then `launches` (1..100) launches timed with CUDA events.
- * Writes the fastest launch's rate to *tflops in TFLOP/s (one FMA = 2 flops).
+ * call times a kernel of independent FMA chains on the current device (8 per
+ * thread, 4 blocks of 256 threads per SM, about 16 ms per launch on a GPU with
+ * two float64 FMAs per clock per SM) on a stream of its own, one untimed launch
+ * and then `launches` (1..100) launches timed with CUDA events, and writes the
+ * fastest launch's rate to *tflops in TFLOP/s (one FMA = 2 flops).  The figure
+ * is a lower bound on the float64 pipe's rate, not its peak: on GB300 it reads
+ * about 0.84 of the nominal two FMAs per clock per SM, and long launches of the
+ * float64 operator run faster than it.
  * Allocates and frees a small device buffer; synchronises its own stream.
  * Returns MG_ERR_ARG for launches outside 1..100 or a null tflops, MG_ERR_CUDA
  * if a CUDA call fails. */

@@ -1,12 +1,13 @@
-// Float64 FMA throughput of the current device: the rate that bounds the
+// Float64 FMA throughput of the current device, the unit that bounds the
 // outer Krylov operator (eight float64 FMAs per finest point, one neighbour
-// load each), on GPUs whose float64 pipe is narrow.  A measurement helper for
-// roofline figures; no solve calls it.
+// load each) on GPUs whose float64 pipe is narrow.  A measurement helper for
+// roofline figures; no solve calls it.  What it times is a lower bound on the
+// pipe's rate: on GB300 long launches of the float64 operator run faster.
 //
 // Every thread runs PK_CHAINS independent recurrences a <- a * m + c, so the
-// float64 pipe always has independent instructions to issue and the latency of
-// one FMA never limits the rate.  With m = 1 - 2^-10 and c = 2^-10 every chain
-// stays in [1, 2) (its fixed point is 1): no overflow, no subnormals.
+// float64 pipe has independent instructions to issue.  With m = 1 - 2^-10 and
+// c = 2^-10 every chain stays in [1, 2) (its fixed point is 1): no overflow,
+// no subnormals.
 #include <cuda_runtime.h>
 
 #include <algorithm>

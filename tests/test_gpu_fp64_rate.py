@@ -1,10 +1,10 @@
 """The float64 FMA-rate probe (mg_fp64_fma_peak), through the C ABI.
 
 The outer Krylov operator is bound by the float64 FMA rate; bench.py reports
-this probe's measured rate beside the rate derived from unit counts and the
-SM clock.  The check here is that the probe runs and returns a rate between
-a tenth of a TFLOP/s and what the widest float64 pipe (64 FMAs per clock per
-SM) could reach at 3 GHz.
+this probe's rate (a lower bound on the float64 pipe's) beside the peak
+derived from unit counts and the SM clock.  The check here is that the probe
+runs and returns a rate between a tenth of a TFLOP/s and what the widest
+float64 pipe (64 FMAs per clock per SM) could reach at 3 GHz.
 """
 import ctypes
 
